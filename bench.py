@@ -1,0 +1,436 @@
+"""Benchmark: edge_metrics forward + adjoint on the 160^3 x 6 tetrahedral grid.
+
+One step = the whole hot path over the whole grid: lumped directed-area
+vectors, dual volumes and boundary normals (forward) plus dL/dx for
+L = sum w.n + sum c V (adjoint), with the topology built once beforehand
+(edge_build, gather plan), as in a deforming-grid time loop.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+N > 1 is launched with torch.distributed.run; every rank runs an independent
+replica of the workload on its own GPU (the metric computation has no
+exchange step), so the scaling is weak and the value is the elements of all
+ranks divided by the slowest rank's time.  Prints ONE JSON line on rank 0.
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen  # noqa: E402
+
+METRIC = "edge_metrics fwd+adjoint elements/s (achieved HBM GB/s vs peak in roofline)"
+UNIT = "elements/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="kuhn160_off1e3")
+    p.add_argument("--path", default=None, help="atomic | gather (default: fastest available)")
+    p.add_argument("--prec", default=None, help="fp64 | dw | mixed")
+    p.add_argument("--tile-nodes", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the per-form comparison timings")
+    p.add_argument("--cpu-sample-elems", type=int, default=1_500_000)
+    p.add_argument("--cpu-reps", type=int, default=4)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_mesh(name):
+    cache = os.environ.get("EM_MESH_CACHE") or os.path.join(ROOT, "_build", "meshcache")
+    return meshgen.generate.cached_workload(name, cache_dir=cache)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes (compulsory traffic: every input read once, every output
+# written once)
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(m, topo, what, path):
+    ne, nv, nE = m.n_elems, m.n_nodes, topo.n_edges
+    nb, nbn, d = topo.n_bfaces, topo.n_bnodes, m.dim
+    nle = 6 if d == 3 else 3
+    mesh_in = 16 * ne + 4 * nle * ne + 8 * d * nv + (4 * d + 4) * nb + 4 * nbn   # elems, elem2edge, x, bfaces
+    fwd_out = 8 * d * nE + 8 * nv + 8 * d * nbn
+    adj_in = 8 * d * nE + 8 * nv                                                  # w, c
+    adj_out = 8 * d * nv
+    if what == "fwd":
+        return mesh_in + fwd_out
+    if what == "adj":
+        return mesh_in + adj_in + adj_out
+    return mesh_in + fwd_out + adj_in + adj_out                                   # fused
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    the summary was taken on the current source of that kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        j = json.load(open(p))
+        ent = j.get(kernel)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, ent["source"])
+        import hashlib
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if h != ent.get("source_sha1"):
+            return None
+        return ent["dram_bytes_per_launch"] * ent.get("scale_to_full", 1.0)
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (baseline / reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(m, n_elems):
+    import oracle
+    sub = m.elems[:min(n_elems, m.n_elems)]
+    used = np.unique(sub[:, :m.dim + 1].ravel())
+    remap = np.full(m.n_nodes, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    el = sub.copy()
+    el[:, :m.dim + 1] = remap[sub[:, :m.dim + 1]]
+    x = np.ascontiguousarray(m.x[used])
+    topo = oracle.topology(m.dim, el, x)
+    w, c = meshgen.generate.loss_weights(topo.n_edges, x.shape[0], m.dim)
+    return el, x, topo, w, c
+
+
+def oracle_time(m, n_elems, reps):
+    import oracle
+    el, x, topo, w, c = oracle_sample(m, n_elems)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.direct(m.dim, x, el, topo)
+        oracle.adjoint(m.dim, x, el, topo, w, c)
+    dt = time.perf_counter() - t0
+    return el.shape[0] * reps / dt, dt, el.shape[0]
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    m = load_mesh(args.workload)
+    import oracle
+    el, x, topo, w, c = oracle_sample(m, args.cpu_sample_elems)
+    for _ in range(args.warmup):
+        oracle.direct(m.dim, x, el, topo)
+        oracle.adjoint(m.dim, x, el, topo, w, c)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.direct(m.dim, x, el, topo)
+        oracle.adjoint(m.dim, x, el, topo, w, c)
+        times.append(time.perf_counter() - t0)
+    per_step = float(np.mean(times))
+    value = el.shape[0] / per_step
+    sample = (f"first {el.shape[0]} of {m.n_elems} Morton-ordered elements of {args.workload} "
+              f"(a contiguous sub-grid), forward + adjoint per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "elements": m.n_elems, "nodes": m.n_nodes},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2502_00778_gb300 import api, load
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = load()
+
+    m = load_mesh(args.workload)
+    x = torch.from_numpy(m.x).to(dev)
+    el = torch.from_numpy(m.elems).to(dev)
+    topo = api.edge_build(el, x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    topo2 = api.edge_build(el, x)
+    torch.cuda.synchronize()
+    edge_build_ms = (time.perf_counter() - t0) * 1e3
+    del topo2
+    have_gather = True
+    try:
+        t0 = time.perf_counter()
+        api.plan_build(topo, args.tile_nodes)
+        torch.cuda.synchronize()
+        plan_build_ms = (time.perf_counter() - t0) * 1e3
+    except Exception:
+        have_gather = False
+        plan_build_ms = None
+    path = args.path or ("gather" if have_gather else "atomic")
+    prec = args.prec or ("dw" if path == "gather" else "fp64")
+
+    g = torch.Generator(device="cpu").manual_seed(meshgen.SEED_BASE + 5)
+    w = torch.randn((topo.n_edges, m.dim), generator=g, dtype=torch.float64).to(dev)
+    c = torch.randn(m.n_nodes, generator=g, dtype=torch.float64).to(dev)
+    outs = (torch.empty((topo.n_edges, m.dim), dtype=torch.float64, device=dev),
+            torch.empty(m.n_nodes, dtype=torch.float64, device=dev),
+            torch.empty((topo.n_bnodes, m.dim), dtype=torch.float64, device=dev),
+            torch.empty((m.n_nodes, m.dim), dtype=torch.float64, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step(x_, w_, c_, ev=None):
+        if path == "gather":
+            if ev is not None:
+                ev[0].record(stream)
+            api.edge_metrics_fused(topo, x_, w_, c_, prec, out=outs)
+            if ev is not None:
+                ev[1].record(stream)
+        else:
+            if ev is not None:
+                ev[0].record(stream)
+            api.edge_metrics(topo, x_, prec, path, out=outs[:3])
+            if ev is not None:
+                ev[1].record(stream)
+            api.edge_metrics_adjoint(topo, x_, w_, c_, prec if prec != "mixed_comp32" else "mixed", path,
+                                     out=outs[3])
+            if ev is not None:
+                ev[2].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step(x, w, c)
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM (all larger than L2) ----
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.em_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler attach
+    start.record(stream)
+    for i in range(K):
+        step(x, w, c, evs[i])
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = L.em_kernel_launches() - launches0
+    if ws > 1:
+        dist.barrier()
+    total_ms = start.elapsed_time(end)
+    t_max = total_ms
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / K
+    value = ws * m.n_elems * K / (t_max * 1e-3)
+
+    # dominant kernel: the fused gather kernel, or the forward element kernel
+    if path == "gather":
+        call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
+        what, kname = "fused", f"k_tile_fused<{prec}>"
+    else:
+        call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
+        what, kname = "fwd", f"k_fwd_atomic3<{prec}>"
+    kern_ms = float(np.mean(call_ms))
+    ab = algorithmic_bytes(m, topo, what, path)
+    peak, peak_kind = peaks()
+    achieved = ab / (kern_ms * 1e-3) / 1e9
+    traffic = kernel_traffic(kname)
+    step_bytes = algorithmic_bytes(m, topo, "fused", path)
+
+    # ---- end to end through the public API with host buffers ----
+    xh = torch.from_numpy(m.x).pin_memory()
+    wh = w.cpu().pin_memory()
+    ch = c.cpu().pin_memory()
+    oh = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    xd, wd, cd = torch.empty_like(x), torch.empty_like(w), torch.empty_like(c)
+    h2d = xh.numel() * 8 + wh.numel() * 8 + ch.numel() * 8
+    d2h = sum(o.numel() * 8 for o in oh)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        wd.copy_(wh, non_blocking=True)
+        cd.copy_(ch, non_blocking=True)
+        step(xd, wd, cd)
+        for o, hbuf in zip(outs, oh):
+            hbuf.copy_(o, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ke = max(3, K // 4)
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = ws * m.n_elems / (e2e_ms * 1e-3)
+
+    # ---- per-form comparison (same workload, separate short timings) ----
+    forms = {}
+    if not args.no_forms and rank == 0:
+        cand = [("atomic", "fp64"), ("atomic", "mixed")]
+        if have_gather:
+            cand += [("gather", "fp64"), ("gather", "dw"), ("gather", "mixed")]
+        for pth, pr in cand:
+            try:
+                def fstep():
+                    if pth == "gather":
+                        api.edge_metrics_fused(topo, x, w, c, pr, out=outs)
+                    else:
+                        api.edge_metrics(topo, x, pr, pth, out=outs[:3])
+                        api.edge_metrics_adjoint(topo, x, w, c, pr, pth, out=outs[3])
+                for _ in range(2):
+                    fstep()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 5
+                a.record(stream)
+                for _ in range(reps):
+                    fstep()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / reps
+                forms[f"{pth}/{pr}"] = {"ms_per_step": round(ms, 4), "elements_per_s": m.n_elems / (ms * 1e-3),
+                                        "algorithmic_GBs": step_bytes / (ms * 1e-3) / 1e9}
+            except Exception as ex:  # a form that is not built reports why
+                forms[f"{pth}/{pr}"] = {"unavailable": str(ex)[:120]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt, ns = oracle_time(m, args.cpu_sample_elems, args.cpu_reps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {ns} Morton-ordered elements of {args.workload}, forward + adjoint, "
+                         f"{args.cpu_reps} repetitions ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "dw": "f32x2+i64 (FP64-accurate)", "mixed": "f32",
+                      "mixed_comp32": "f32"}.get(prec, prec),
+            "data": "synthetic",
+            "config": {"workload": args.workload, "elements": m.n_elems, "nodes": m.n_nodes, "edges": topo.n_edges,
+                       "path": path, "precision": prec, "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (no flush needed)", "tile_nodes": args.tile_nodes},
+            "hbm_gbs_step": step_bytes / (ms_per_step * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                         "kernel_ms": kern_ms, "algorithmic_bytes": ab, "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "edge_build_ms": edge_build_ms, "plan_build_ms": plan_build_ms,
+            "forms": forms,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

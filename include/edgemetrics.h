@@ -1,0 +1,269 @@
+/*
+ * edgemetrics.h -- C ABI of the GB300 (sm_103a) edge-metrics library.
+ *
+ * The library computes, on triangular (dim = 2) and tetrahedral (dim = 3)
+ * grids, the grid metrics of the edge-based finite-volume discretization
+ * directly from element geometry, without forming median-dual control
+ * volumes (H. Nishikawa, arXiv 2502.00778):
+ *
+ *   n_e      lumped directed-area vector of every edge e = {j,k}, j < k,
+ *            pointing from j to k (Sec. 2).  Proposed algorithm, Sec. 3.2:
+ *            n_jk = 2/(D(D+1)) sum_{E containing jk} n_j^E  plus
+ *            n_B/(D(D+1)) for every boundary face B containing jk
+ *            (Eq. efficient_njk_formula_general_D and the boundary
+ *            correction after it), where n_j^E is the outward area vector of
+ *            the face of E opposite j and n_B the outward area vector of B.
+ *   V_i      median-dual volume of every node: sum over elements E of
+ *            V_E/(D+1) (Sec. 4.2).
+ *   b_i      boundary dual-face normal of every boundary node:
+ *            (1/D) sum_{B containing i} n_B (Sec. 3.2.3, closure).
+ *   dL/dx    gradient of L = sum_e w_e . n_e + sum_i c_i V_i with respect to
+ *            the node coordinates (the adjoint of the above).
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is a DEVICE pointer owned by the caller unless
+ *     stated otherwise; the library never allocates or frees caller memory.
+ *   - Temporary storage is a caller-provided device workspace: call once with
+ *     ws == NULL to receive the required size in *ws_bytes, then call again
+ *     with a buffer of at least that size (256-byte aligned).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All work is enqueued on it.  Entry points that must
+ *     return a count to the host (em_edge_build, em_plan_build) synchronize
+ *     the stream before returning; all others are asynchronous.
+ *   - Element connectivity is int32 [n_elems][4]; triangles use the first
+ *     three entries and store -1 in the fourth.  Node ids are 0-based.
+ *   - Coordinates are float64 [n_nodes][dim], row-major.
+ *   - Node, element, edge and face counts must be below 2^31 - 1 (int32
+ *     indices); byte offsets are size_t.
+ *   - Every function returns an int status: EM_OK (0) or a negative EM_ERR_*
+ *     code.  em_last_error() returns a message for the calling thread's last
+ *     failure.  No C++ exception crosses the ABI and no kernel traps: device-
+ *     side failures (bad ids, degenerate elements, timeouts) are reported
+ *     through a status word that the host reads.
+ */
+#ifndef EDGEMETRICS_H
+#define EDGEMETRICS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EM_VERSION 100
+
+/* status codes */
+#define EM_OK               0
+#define EM_ERR_ARG         -1   /* invalid argument (null pointer, bad size, unsupported dim/mode) */
+#define EM_ERR_WORKSPACE   -2   /* workspace missing or smaller than required */
+#define EM_ERR_CUDA        -3   /* a CUDA runtime call failed */
+#define EM_ERR_BAD_ID      -4   /* element references a node id outside [0,n_nodes) or repeats a node */
+#define EM_ERR_DEGENERATE  -5   /* an element has zero measure */
+#define EM_ERR_TIMEOUT     -6   /* a bounded device-side wait gave up */
+#define EM_ERR_CAPACITY    -7   /* an output capacity (edges_cap, ...) is too small */
+#define EM_ERR_TOPOLOGY    -8   /* a face is shared by more than two elements */
+
+/* arithmetic forms */
+#define EM_PREC_FP64   0  /* native double-precision arithmetic and FP64 accumulation */
+#define EM_PREC_DW     1  /* FP64-accurate results computed without FP64 instructions:
+                             exact coordinate differences, FP32 double-word (error-free
+                             transformation) products, exact integer accumulation */
+#define EM_PREC_MIXED  2  /* FP32 element arithmetic on element-relative coordinates
+                             (rounding ~1e-7 relative); accumulation exact (gather path)
+                             or FP64 atomics (atomic path) */
+#define EM_PREC_MIXED_COMP32 3 /* atomic path only: FP32 element arithmetic with
+                             compensated FP32 (two-float) atomic accumulation */
+
+/* summation paths */
+#define EM_PATH_ATOMIC 0  /* element-centric scatter with global FP64 atomics
+                             (summation order not reproducible) */
+#define EM_PATH_GATHER 1  /* tiled gather: every output written once, exact integer
+                             accumulation; bit-reproducible run to run */
+#define EM_PATH_CSR    2  /* edge-centric CSR gather (per edge, its element slots in
+                             ascending order; FP64 only); bit-reproducible */
+
+int em_version(void);
+
+/* Number of CUDA kernels this library has enqueued in the calling process
+ * (all threads, all devices) since it was loaded; a diagnostic for
+ * benchmarks.  Memset and copy operations are not counted. */
+int64_t em_kernel_launches(void);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to n bytes) into buf; returns the last status code. */
+int em_last_error(char* buf, size_t n);
+
+/* ------------------------------------------------------------------------ */
+/* Topology                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* em_edge_build -- integer topology of a grid (run once per connectivity).
+ *
+ * Edges (Sec. 2: edge(e,1) = j < edge(e,2) = k) are all element edges, sorted
+ * lexicographically by (j,k); they are found by a radix sort of 64-bit
+ * (min,max) keys and a unique pass.  Results are bit-exact.
+ *
+ *   elems        [n_elems][4] int32, read.
+ *   x            [n_nodes][dim] float64, read: only used to orient boundary
+ *                faces outward.
+ *   edges        [edges_cap][2] int32, written: edges[e] = {j, k}, j < k.
+ *   elem2edge    [n_elems][nle] int32, written (nle = 6 for tets, 3 for
+ *                tris): edge id of local edge l, local edges taken over the
+ *                STORED node order as (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
+ *                (tris: (0,1),(0,2),(1,2)).
+ *   edge_ptr     [edges_cap+1] int32 or NULL, written: CSR offsets of each
+ *                edge's element slots.
+ *   edge_slot    [n_elems*nle] int32 or NULL, written: slots e*nle+l, grouped
+ *                by edge, ascending inside each edge.
+ *   bface        [bface_cap][dim] int32, written: faces seen by exactly one
+ *                element (the boundary elements of Sec. 3.2, taken as given in
+ *                the paper), sorted by their sorted node ids, stored in the
+ *                order that makes n_B outward (3D: first node = smallest id,
+ *                n_B = 1/2 (x1-x0) x (x2-x0); 2D: n_B = (y0-y1, x1-x0)).
+ *   bface_owner  [bface_cap] int32, written: elem*4 + local index of the
+ *                owner's node opposite the face.
+ *   bnode        [bnode_cap] int32, written: ascending ids of nodes on
+ *                boundary faces.
+ *   counts       HOST int64[3], written: n_edges, n_bfaces, n_bnodes.
+ *
+ * Capacities: edges_cap >= number of edges (at most nle*n_elems), bface_cap
+ * >= number of boundary faces (at most (dim+1)*n_elems), bnode_cap >= number
+ * of boundary nodes (at most n_nodes); otherwise EM_ERR_CAPACITY and the
+ * needed counts are still written to `counts`.  Synchronizes `stream`.
+ * Errors: EM_ERR_BAD_ID, EM_ERR_TOPOLOGY, EM_ERR_CAPACITY, EM_ERR_ARG,
+ * EM_ERR_WORKSPACE, EM_ERR_CUDA. */
+int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
+                  const int32_t* elems, const double* x,
+                  void* ws, size_t* ws_bytes,
+                  int32_t* edges, int64_t edges_cap,
+                  int32_t* elem2edge,
+                  int32_t* edge_ptr, int32_t* edge_slot,
+                  int32_t* bface, int32_t* bface_owner, int64_t bface_cap,
+                  int32_t* bnode, int64_t bnode_cap,
+                  int64_t* counts,
+                  void* stream);
+
+/* em_plan_build -- tiled gather plan for EM_PATH_GATHER (run once per
+ * connectivity, after em_edge_build).
+ *
+ * Nodes are cut into tiles of `tile_nodes` consecutive ids (a spatially
+ * compact numbering, such as Morton order, keeps tiles compact).  A tile owns
+ * its nodes, the edges whose lower end it owns and the boundary nodes among
+ * its nodes; it processes every element and boundary face that touches one of
+ * its nodes, so every output is produced by exactly one tile.
+ *
+ *   plan         device buffer of *plan_bytes bytes, written; call with
+ *                plan == NULL to query the size (an upper bound from the
+ *                counts; the bound needs no device work).
+ *   tile_nodes   nodes per tile, 32..2048, multiple of 32 (0 = default 512).
+ * The plan stores device pointers to nothing: it is position-independent and
+ * may be copied.  Synchronizes `stream`. */
+int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems,
+                  const int32_t* elem2edge,
+                  int64_t n_edges, const int32_t* edges,
+                  int64_t n_bfaces, const int32_t* bface, const int32_t* bface_owner,
+                  int64_t n_bnodes, const int32_t* bnode,
+                  int tile_nodes,
+                  void* ws, size_t* ws_bytes,
+                  void* plan, size_t* plan_bytes,
+                  void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Metrics                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Mesh description passed to the metric entry points: device pointers from
+ * em_edge_build (and em_plan_build for EM_PATH_GATHER). */
+typedef struct em_mesh {
+    int dim;
+    int64_t n_nodes, n_elems, n_edges, n_bfaces, n_bnodes;
+    const int32_t* elems;        /* [n_elems][4] */
+    const int32_t* elem2edge;    /* [n_elems][nle] */
+    const int32_t* edges;        /* [n_edges][2] */
+    const int32_t* edge_ptr;     /* [n_edges+1], needed by EM_PATH_CSR only */
+    const int32_t* edge_slot;    /* [n_elems*nle], needed by EM_PATH_CSR only */
+    const int32_t* bface;        /* [n_bfaces][dim] */
+    const int32_t* bface_owner;  /* [n_bfaces] */
+    const int32_t* bnode;        /* [n_bnodes] */
+    const void* plan;            /* from em_plan_build, needed by EM_PATH_GATHER only */
+    size_t plan_bytes;
+} em_mesh;
+
+/* em_edge_metrics -- forward: n_edge [n_edges][dim], vol [n_nodes],
+ * bnormal [n_bnodes][dim] (all overwritten; any may be NULL to skip it on
+ * the atomic path, all three are always produced on the gather paths).
+ *   x          [n_nodes][dim] float64.
+ *   precision  EM_PREC_*; path EM_PATH_*.  Supported pairs: ATOMIC with FP64,
+ *              MIXED, MIXED_COMP32; GATHER with FP64, DW, MIXED; CSR with FP64.
+ * Errors: EM_ERR_ARG (unsupported pair, missing plan/CSR), EM_ERR_WORKSPACE,
+ * EM_ERR_CUDA.  Degenerate elements are not checked here (see
+ * em_check_elements). */
+int em_edge_metrics(const em_mesh* mesh, int precision, int path,
+                    const double* x,
+                    double* n_edge, double* vol, double* bnormal,
+                    void* ws, size_t* ws_bytes, void* stream);
+
+/* em_edge_metrics_adjoint -- grad_x [n_nodes][dim] (overwritten) =
+ * d/dx ( sum_e w[e] . n_e + sum_i c[i] V_i ), w [n_edges][dim], c [n_nodes]
+ * (c may be NULL: treated as zero).  Boundary dual-face normals are not part
+ * of L.  Supported pairs: ATOMIC with FP64 or MIXED; GATHER with FP64, DW,
+ * MIXED. */
+int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path,
+                            const double* x, const double* w, const double* c,
+                            double* grad_x,
+                            void* ws, size_t* ws_bytes, void* stream);
+
+/* em_edge_metrics_fused -- forward outputs and the adjoint in one pass over
+ * the grid (the adjoint does not depend on the forward outputs).  GATHER path
+ * only (FP64, DW, MIXED). */
+int em_edge_metrics_fused(const em_mesh* mesh, int precision,
+                          const double* x, const double* w, const double* c,
+                          double* n_edge, double* vol, double* bnormal, double* grad_x,
+                          void* ws, size_t* ws_bytes, void* stream);
+
+/* em_check_elements -- validation: counts elements with a node id outside
+ * [0,n_nodes), a repeated node, or zero measure (det == 0 in FP64).
+ *   ws       device workspace (size query with ws == NULL, as everywhere).
+ *   counts   HOST int64[2] = {bad ids, degenerate}.
+ * Returns EM_ERR_BAD_ID / EM_ERR_DEGENERATE when the respective count is
+ * non-zero (degeneracy is only tested when every id is valid).
+ * Synchronizes `stream`. */
+int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems,
+                      const double* x, void* ws, size_t* ws_bytes, int64_t* counts, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched meshes                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* One mesh of a batch: everything em_edge_metrics_fused needs (GATHER plan
+ * required) plus its inputs and outputs. */
+typedef struct em_batch_item {
+    em_mesh mesh;
+    const double* x; const double* w; const double* c;
+    double* n_edge; double* vol; double* bnormal; double* grad_x;
+} em_batch_item;
+
+/* em_batched_fwd_adj -- forward + adjoint for n_meshes meshes of uneven size
+ * in ONE persistent launch: the tiles of all meshes form one work list that
+ * resident blocks drain through an atomic counter.
+ *   items       DEVICE array [n_meshes] of em_batch_item (pointers inside are
+ *               device pointers).
+ *   tile_prefix DEVICE int64 [n_meshes+1]: exclusive prefix sum of the meshes'
+ *               tile counts (from em_plan_tiles()).
+ *   blocks      persistent grid size (0 = number of SMs x resident blocks).
+ *   status      DEVICE int32[1], written: 0 or a negative EM_ERR_* code.
+ * Holds no host-side state, makes no allocation and performs no
+ * synchronization, so the call can be captured in a CUDA graph once its
+ * workspace is allocated.  Precision: FP64, DW or MIXED. */
+int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix,
+                       int precision, int blocks, int32_t* status,
+                       void* ws, size_t* ws_bytes, void* stream);
+
+/* number of tiles in a plan (HOST read of the plan header; synchronizes) */
+int em_plan_tiles(const void* plan, int64_t* n_tiles, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDGEMETRICS_H */

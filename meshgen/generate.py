@@ -104,7 +104,8 @@ def _scramble(rng, x, el, dim, permute_nodes=True, permute_elems=True, permute_l
     if permute_elems:
         el = el[rng.permutation(ne)]
     if permute_local:
-        order = np.argsort(rng.random((ne, k)), axis=1)
+        perms = np.array(list(itertools.permutations(range(k))), dtype=np.int64)
+        order = perms[rng.integers(0, perms.shape[0], size=ne)]
         el = el.copy()
         el[:, :k] = np.take_along_axis(el[:, :k], order, axis=1)
     return x, el
@@ -152,7 +153,10 @@ def _morton_reorder(x, el, dim):
     k = dim + 1
     el = el.copy()
     el[:, :k] = rank[el[:, :k]]
-    cen = x[el[:, :k]].mean(axis=1)
+    cen = x[el[:, 0]]
+    for i in range(1, k):
+        cen = cen + x[el[:, i]]
+    cen *= 1.0 / k
     el = el[np.argsort(_morton_keys(cen, lo, hi), kind="stable")]
     return np.ascontiguousarray(x), el
 
@@ -276,4 +280,33 @@ def workload(name: str, **override) -> Mesh:
     kw.update(override)
     m = fn(**kw)
     m.name = name
+    return m
+
+
+# ----------------------------------------------------------------------------
+# optional on-disk cache (a directory named by EM_MESH_CACHE, or none)
+# ----------------------------------------------------------------------------
+def cached_workload(name: str, cache_dir: str = None, **override) -> Mesh:
+    """workload(name) with an .npz cache, so separate processes of one run
+    (tests, benchmark) generate the large grids only once."""
+    import hashlib
+    import json
+    import os
+    cache_dir = cache_dir or os.environ.get("EM_MESH_CACHE")
+    if not cache_dir:
+        return workload(name, **override)
+    fn, kw = WORKLOADS[name]
+    kw = dict(kw)
+    kw.update(override)
+    tag = hashlib.sha1(json.dumps([name, fn.__name__, sorted(kw.items())], default=str).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir, f"{name}-{tag}.npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        meta = json.loads(str(z["meta"]))
+        return Mesh(name=name, dim=int(z["dim"]), x=z["x"], elems=z["elems"], h=float(z["h"]), meta=meta)
+    m = workload(name, **override)
+    os.makedirs(cache_dir, exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, x=m.x, elems=m.elems, dim=m.dim, h=m.h, meta=json.dumps(m.meta))
+    os.replace(tmp, path)
     return m

@@ -1,0 +1,275 @@
+"""Python binding of the edge-metrics library: argument marshalling only.
+
+PyTorch provides device memory and the current CUDA stream; every step of
+the computation runs in the library's CUDA kernels.  Tensors passed in must
+live on the GPU; nothing here falls back to a CPU implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import EmMesh, PATH, PREC, check, load
+
+__all__ = ["Topology", "edge_build", "plan_build", "edge_metrics", "edge_metrics_adjoint", "edge_metrics_fused",
+           "check_elements", "EdgeMetrics", "workspace"]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _Workspace:
+    """Grow-only device workspace shared by calls on one device."""
+
+    def __init__(self):
+        self.buf = {}
+
+    def get(self, nbytes, device):
+        key = str(device)
+        b = self.buf.get(key)
+        if b is None or b.numel() < nbytes:
+            b = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+            self.buf[key] = b
+        return b
+
+
+workspace = _Workspace()
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("edge-metrics tensors must be CUDA tensors")
+
+
+class Topology:
+    """Integer topology from em_edge_build (+ optional gather plan)."""
+
+    def __init__(self, dim, elems, edges, elem2edge, edge_ptr, edge_slot, bface, bface_owner, bnode, n_nodes):
+        self.dim = dim
+        self.n_nodes = n_nodes
+        self.elems = elems
+        self.edges = edges
+        self.elem2edge = elem2edge
+        self.edge_ptr = edge_ptr
+        self.edge_slot = edge_slot
+        self.bface = bface
+        self.bface_owner = bface_owner
+        self.bnode = bnode
+        self.plan = None
+        self.tile_nodes = None
+
+    @property
+    def n_elems(self):
+        return self.elems.shape[0]
+
+    @property
+    def n_edges(self):
+        return self.edges.shape[0]
+
+    @property
+    def n_bfaces(self):
+        return self.bface.shape[0]
+
+    @property
+    def n_bnodes(self):
+        return self.bnode.shape[0]
+
+    def em_mesh(self) -> EmMesh:
+        m = EmMesh()
+        m.dim = self.dim
+        m.n_nodes, m.n_elems, m.n_edges = self.n_nodes, self.n_elems, self.n_edges
+        m.n_bfaces, m.n_bnodes = self.n_bfaces, self.n_bnodes
+        m.elems = self.elems.data_ptr()
+        m.elem2edge = self.elem2edge.data_ptr()
+        m.edges = self.edges.data_ptr()
+        m.edge_ptr = self.edge_ptr.data_ptr() if self.edge_ptr is not None else None
+        m.edge_slot = self.edge_slot.data_ptr() if self.edge_slot is not None else None
+        m.bface = self.bface.data_ptr() if self.n_bfaces else None
+        m.bface_owner = self.bface_owner.data_ptr() if self.n_bfaces else None
+        m.bnode = self.bnode.data_ptr() if self.n_bnodes else None
+        m.plan = self.plan.data_ptr() if self.plan is not None else None
+        m.plan_bytes = self.plan.numel() if self.plan is not None else 0
+        return m
+
+
+def edge_build(elems: torch.Tensor, x: torch.Tensor, csr: bool = True) -> Topology:
+    """Edges, element->edge map, CSR, boundary faces and nodes (bit-exact)."""
+    L = load()
+    _require_cuda(elems, x)
+    elems = elems.contiguous().to(torch.int32)
+    x = x.contiguous().to(torch.float64)
+    ne = elems.shape[0]
+    nv, dim = x.shape
+    nle = 6 if dim == 3 else 3
+    dev = elems.device
+    wsb = ctypes.c_size_t(0)
+    counts = (ctypes.c_int64 * 3)()
+    null = ctypes.c_void_p(0)
+    check(L.em_edge_build(dim, nv, ne, _ptr(elems), _ptr(x), null, ctypes.byref(wsb), null, 0, null, null, null, null,
+                          null, 0, null, 0, counts, _stream()))
+    ws = workspace.get(wsb.value, dev)
+    cap_e = nle * ne
+    cap_b = (dim + 1) * ne
+    edges = torch.empty((cap_e, 2), dtype=torch.int32, device=dev)
+    e2e = torch.empty((ne, nle), dtype=torch.int32, device=dev)
+    eptr = torch.empty(cap_e + 1, dtype=torch.int32, device=dev) if csr else None
+    eslot = torch.empty(nle * ne, dtype=torch.int32, device=dev) if csr else None
+    bface = torch.empty((cap_b, dim), dtype=torch.int32, device=dev)
+    bown = torch.empty(cap_b, dtype=torch.int32, device=dev)
+    bnode = torch.empty(nv, dtype=torch.int32, device=dev)
+    check(L.em_edge_build(dim, nv, ne, _ptr(elems), _ptr(x), _ptr(ws), ctypes.byref(wsb), _ptr(edges), cap_e,
+                          _ptr(e2e), _ptr(eptr), _ptr(eslot), _ptr(bface), _ptr(bown), cap_b, _ptr(bnode), nv,
+                          counts, _stream()))
+    n_e, n_b, n_bn = counts[0], counts[1], counts[2]
+    topo = Topology(dim, elems, edges[:n_e].clone(), e2e, eptr[:n_e + 1].clone() if csr else None, eslot,
+                    bface[:n_b].clone(), bown[:n_b].clone(), bnode[:n_bn].clone(), nv)
+    return topo
+
+
+def plan_build(topo: Topology, tile_nodes: int = 0) -> Topology:
+    """Build the tiled gather plan (EM_PATH_GATHER) into topo.plan."""
+    L = load()
+    dev = topo.elems.device
+    wsb = ctypes.c_size_t(0)
+    pb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    args = (topo.dim, topo.n_nodes, topo.n_elems, _ptr(topo.elems), _ptr(topo.elem2edge), topo.n_edges,
+            _ptr(topo.edges), topo.n_bfaces, _ptr(topo.bface) if topo.n_bfaces else null,
+            _ptr(topo.bface_owner) if topo.n_bfaces else null, topo.n_bnodes,
+            _ptr(topo.bnode) if topo.n_bnodes else null, int(tile_nodes))
+    check(L.em_plan_build(*args, null, ctypes.byref(wsb), null, ctypes.byref(pb), _stream()))
+    ws = workspace.get(wsb.value, dev)
+    plan = torch.empty(max(pb.value, 256), dtype=torch.uint8, device=dev)
+    check(L.em_plan_build(*args, _ptr(ws), ctypes.byref(wsb), _ptr(plan), ctypes.byref(pb), _stream()))
+    topo.plan = plan[:pb.value] if pb.value <= plan.numel() else plan
+    topo.tile_nodes = tile_nodes
+    return topo
+
+
+def plan_tiles(topo: Topology) -> int:
+    n = ctypes.c_int64(0)
+    check(load().em_plan_tiles(_ptr(topo.plan), ctypes.byref(n), _stream()))
+    return n.value
+
+
+def _mesh_ref(topo):
+    m = topo.em_mesh()
+    return m, ctypes.byref(m)
+
+
+def edge_metrics(topo: Topology, x: torch.Tensor, precision: str = "fp64", path: str = "atomic", out=None):
+    """Forward: (n_edge [Ne,dim], vol [Nv], bnormal [Nbn,dim]) as float64 CUDA tensors."""
+    L = load()
+    _require_cuda(x)
+    x = x.contiguous().to(torch.float64)
+    dim, dev = topo.dim, x.device
+    if out is None:
+        n = torch.empty((topo.n_edges, dim), dtype=torch.float64, device=dev)
+        v = torch.empty(topo.n_nodes, dtype=torch.float64, device=dev)
+        b = torch.empty((topo.n_bnodes, dim), dtype=torch.float64, device=dev)
+    else:
+        n, v, b = out
+    m, mr = _mesh_ref(topo)
+    wsb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    pr, pa = PREC[precision], PATH[path]
+    check(L.em_edge_metrics(mr, pr, pa, _ptr(x), _ptr(n), _ptr(v), _ptr(b), null, ctypes.byref(wsb), _stream()))
+    ws = workspace.get(wsb.value, dev)
+    check(L.em_edge_metrics(mr, pr, pa, _ptr(x), _ptr(n), _ptr(v), _ptr(b), _ptr(ws), ctypes.byref(wsb), _stream()))
+    return n, v, b
+
+
+def edge_metrics_adjoint(topo: Topology, x, w, c=None, precision: str = "fp64", path: str = "atomic", out=None):
+    """grad_x = d/dx (sum w.n + sum c V), float64 [Nv, dim]."""
+    L = load()
+    _require_cuda(x, w, c)
+    x = x.contiguous().to(torch.float64)
+    w = w.contiguous().to(torch.float64)
+    c = c.contiguous().to(torch.float64) if c is not None else None
+    g = out if out is not None else torch.empty((topo.n_nodes, topo.dim), dtype=torch.float64, device=x.device)
+    m, mr = _mesh_ref(topo)
+    wsb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    pr, pa = PREC[precision], PATH[path]
+    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(g), null, ctypes.byref(wsb),
+                                    _stream()))
+    ws = workspace.get(wsb.value, x.device)
+    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(g), _ptr(ws), ctypes.byref(wsb),
+                                    _stream()))
+    return g
+
+
+def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", out=None):
+    """Forward outputs and the adjoint in one pass (gather plan required)."""
+    L = load()
+    _require_cuda(x, w, c)
+    x = x.contiguous().to(torch.float64)
+    w = w.contiguous().to(torch.float64)
+    c = c.contiguous().to(torch.float64) if c is not None else None
+    dim, dev = topo.dim, x.device
+    if out is None:
+        n = torch.empty((topo.n_edges, dim), dtype=torch.float64, device=dev)
+        v = torch.empty(topo.n_nodes, dtype=torch.float64, device=dev)
+        b = torch.empty((topo.n_bnodes, dim), dtype=torch.float64, device=dev)
+        g = torch.empty((topo.n_nodes, dim), dtype=torch.float64, device=dev)
+    else:
+        n, v, b, g = out
+    m, mr = _mesh_ref(topo)
+    wsb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    pr = PREC[precision]
+    args = (_ptr(x), _ptr(w), _ptr(c), _ptr(n), _ptr(v), _ptr(b), _ptr(g))
+    check(L.em_edge_metrics_fused(mr, pr, *args, null, ctypes.byref(wsb), _stream()))
+    ws = workspace.get(wsb.value, dev)
+    check(L.em_edge_metrics_fused(mr, pr, *args, _ptr(ws), ctypes.byref(wsb), _stream()))
+    return n, v, b, g
+
+
+def check_elements(dim: int, elems: torch.Tensor, x: torch.Tensor):
+    """(bad-id count, degenerate count); raises EMError on either."""
+    L = load()
+    elems = elems.contiguous().to(torch.int32)
+    x = x.contiguous().to(torch.float64)
+    wsb = ctypes.c_size_t(0)
+    counts = (ctypes.c_int64 * 2)()
+    null = ctypes.c_void_p(0)
+    check(L.em_check_elements(dim, x.shape[0], elems.shape[0], _ptr(elems), _ptr(x), null, ctypes.byref(wsb), counts,
+                              _stream()))
+    ws = workspace.get(wsb.value, elems.device)
+    check(L.em_check_elements(dim, x.shape[0], elems.shape[0], _ptr(elems), _ptr(x), _ptr(ws), ctypes.byref(wsb),
+                              counts, _stream()))
+    return counts[0], counts[1]
+
+
+class EdgeMetrics(torch.autograd.Function):
+    """(n_edge, vol, bnormal) = EdgeMetrics.apply(x, topo, precision, path).
+
+    backward calls the adjoint kernel with w = grad(n_edge), c = grad(vol);
+    the gradient through bnormal is not propagated (it is not part of L)."""
+
+    @staticmethod
+    def forward(ctx, x, topo, precision="fp64", path="atomic"):
+        ctx.topo, ctx.precision, ctx.path = topo, precision, path
+        ctx.save_for_backward(x)
+        n, v, b = edge_metrics(topo, x, precision, path)
+        ctx.mark_non_differentiable(b)
+        return n, v, b
+
+    @staticmethod
+    def backward(ctx, gn, gv, gb):
+        (x,) = ctx.saved_tensors
+        topo = ctx.topo
+        if gn is None:
+            gn = torch.zeros((topo.n_edges, topo.dim), dtype=torch.float64, device=x.device)
+        adj_path = ctx.path if ctx.path in ("atomic", "gather") else "atomic"
+        g = edge_metrics_adjoint(topo, x, gn, gv, ctx.precision if ctx.precision != "mixed_comp32" else "mixed",
+                                 adj_path)
+        return g, None, None, None

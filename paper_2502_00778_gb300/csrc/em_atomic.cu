@@ -1,0 +1,449 @@
+// EM_PATH_ATOMIC: element-centric scatter with global atomics.
+//
+// One thread per element.  With a, b, c the edge vectors from the element's
+// first stored node and N1 = b x c, N2 = c x a, N3 = a x b, det = a . N1,
+// s = sign(det), the outward area vector of the face opposite stored node i
+// is n_i = -s N_i / 2 (i = 1..3) and n_0 = -(n_1 + n_2 + n_3).  The proposed
+// algorithm (Eq. efficient_njk_formula_general_D) adds 2/(D(D+1)) n_j to edge
+// {j,k}, j the lower global id; the element-based volume (Sec. 4.2) adds
+// |det|/D! /(D+1) to every node.  The boundary correction n_B/(D(D+1)) and
+// the boundary dual-face normal n_B/D (Sec. 3.2.3) come from a second kernel
+// over boundary faces.
+//
+// Adjoint of L = sum_e w_e.n_e + sum_i c_i V_i: with W_i the sum of w over the
+// element's edges whose lower end is node i, A_i = W_i - W_0 and C = sum c_i,
+//   L_E = -(s/12) (A1.N1 + A2.N2 + A3.N3) + C s det / 24          (3D)
+// so, using w.(p x q) = p.(q x w):
+//   dL/da = -(s/12)(A2 x c - A3 x b) + (C s/24) N1
+//   dL/db = -(s/12)(A3 x a - A1 x c) + (C s/24) N2
+//   dL/dc = -(s/12)(A1 x b - A2 x a) + (C s/24) N3,  dL/dx_0 = -(sum).
+// In 2D n_1 = -s (b_y,-b_x), n_2 = -s (-a_y,a_x), factor 1/3, V_E/3 = |det|/6.
+#include "em_common.cuh"
+#include "em_kernels.cuh"
+
+namespace em {
+
+namespace {
+
+__constant__ int c_le3a[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+__constant__ int c_le2a[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+
+__device__ __forceinline__ int vcomp(const int4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+struct d3 { double x, y, z; };
+__device__ __forceinline__ d3 mk(double a, double b, double c) { return {a, b, c}; }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ d3 operator*(double s, d3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 ld3(const double* x, int64_t i) { return {x[3 * i], x[3 * i + 1], x[3 * i + 2]}; }
+
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 tof(d3 a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+
+// compensated FP32 atomic accumulation into (hi, lo)
+__device__ __forceinline__ void comp_add(float* hi, float* lo, float v) {
+    float old = atomicAdd(hi, v);
+    float s = old + v;
+    float bb = s - old;
+    float err = (old - (s - bb)) + (v - bb);
+    atomicAdd(lo, err);
+}
+
+// ---- forward, 3D ----------------------------------------------------------
+template <int PREC>
+__global__ void k_fwd_atomic3(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                              const double* __restrict__ x, double* __restrict__ n, double* __restrict__ vol,
+                              float* __restrict__ nhi, float* __restrict__ nlo, float* __restrict__ vhi,
+                              float* __restrict__ vlo) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        int4 v = reinterpret_cast<const int4*>(elems)[E];
+        d3 p0 = ld3(x, v.x), p1 = ld3(x, v.y), p2 = ld3(x, v.z), p3 = ld3(x, v.w);
+        d3 m[4];
+        double vq;
+        if (PREC == EM_PREC_FP64) {
+            d3 a = p1 - p0, b = p2 - p0, c = p3 - p0;
+            d3 N1 = cross(b, c), N2 = cross(c, a), N3 = cross(a, b);
+            double det = dot(a, N1);
+            double f = det > 0 ? -1.0 / 12.0 : 1.0 / 12.0;
+            m[1] = f * N1; m[2] = f * N2; m[3] = f * N3;
+            m[0] = -1.0 * (m[1] + m[2] + m[3]);
+            vq = fabs(det) * (1.0 / 24.0);
+        } else {
+            // FP32 element arithmetic on coordinates relative to the first node
+            f3 a = tof(p1 - p0), b = tof(p2 - p0), c = tof(p3 - p0);
+            f3 N1 = cross(b, c), N2 = cross(c, a), N3 = cross(a, b);
+            float det = dot(a, N1);
+            float f = det > 0 ? -1.0f / 12.0f : 1.0f / 12.0f;
+            f3 q1 = f * N1, q2 = f * N2, q3 = f * N3;
+            f3 q0 = -1.0f * (q1 + q2 + q3);
+            m[0] = mk(q0.x, q0.y, q0.z); m[1] = mk(q1.x, q1.y, q1.z);
+            m[2] = mk(q2.x, q2.y, q2.z); m[3] = mk(q3.x, q3.y, q3.z);
+            vq = fabsf(det) * (1.0f / 24.0f);
+        }
+        int gid[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int l = 0; l < 6; l++) {
+            int p = c_le3a[l][0], q = c_le3a[l][1];
+            int lo = gid[p] < gid[q] ? p : q;
+            int64_t e = e2e[E * 6 + l];
+            if (PREC == EM_PREC_MIXED_COMP32) {
+                comp_add(nhi + 3 * e, nlo + 3 * e, (float)m[lo].x);
+                comp_add(nhi + 3 * e + 1, nlo + 3 * e + 1, (float)m[lo].y);
+                comp_add(nhi + 3 * e + 2, nlo + 3 * e + 2, (float)m[lo].z);
+            } else {
+                atomicAdd(n + 3 * e, m[lo].x);
+                atomicAdd(n + 3 * e + 1, m[lo].y);
+                atomicAdd(n + 3 * e + 2, m[lo].z);
+            }
+        }
+        if (vol || vhi) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                if (PREC == EM_PREC_MIXED_COMP32) comp_add(vhi + gid[i], vlo + gid[i], (float)vq);
+                else atomicAdd(vol + gid[i], vq);
+            }
+        }
+    }
+}
+
+// ---- forward, 2D ----------------------------------------------------------
+template <int PREC>
+__global__ void k_fwd_atomic2(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                              const double* __restrict__ x, double* __restrict__ n, double* __restrict__ vol,
+                              float* __restrict__ nhi, float* __restrict__ nlo, float* __restrict__ vhi,
+                              float* __restrict__ vlo) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        int4 v = reinterpret_cast<const int4*>(elems)[E];
+        double m[3][2];
+        double vq;
+        double ax = x[2 * int64_t(v.y)] - x[2 * int64_t(v.x)], ay = x[2 * int64_t(v.y) + 1] - x[2 * int64_t(v.x) + 1];
+        double bx = x[2 * int64_t(v.z)] - x[2 * int64_t(v.x)], by = x[2 * int64_t(v.z) + 1] - x[2 * int64_t(v.x) + 1];
+        if (PREC == EM_PREC_FP64) {
+            double det = ax * by - ay * bx;
+            double f = det > 0 ? -1.0 / 3.0 : 1.0 / 3.0;   // n_i/3 with n_1 = -s (b_y,-b_x), n_2 = -s (-a_y,a_x)
+            m[1][0] = f * by; m[1][1] = -f * bx;
+            m[2][0] = -f * ay; m[2][1] = f * ax;
+            m[0][0] = -(m[1][0] + m[2][0]); m[0][1] = -(m[1][1] + m[2][1]);
+            vq = fabs(det) * (1.0 / 6.0);
+        } else {
+            float fax = (float)ax, fay = (float)ay, fbx = (float)bx, fby = (float)by;
+            float det = fax * fby - fay * fbx;
+            float f = det > 0 ? -1.0f / 3.0f : 1.0f / 3.0f;
+            float q1x = f * fby, q1y = -f * fbx, q2x = -f * fay, q2y = f * fax;
+            m[1][0] = q1x; m[1][1] = q1y; m[2][0] = q2x; m[2][1] = q2y;
+            m[0][0] = -(q1x + q2x); m[0][1] = -(q1y + q2y);
+            vq = fabsf(det) * (1.0f / 6.0f);
+        }
+        int gid[3] = {v.x, v.y, v.z};
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            int p = c_le2a[l][0], q = c_le2a[l][1];
+            int lo = gid[p] < gid[q] ? p : q;
+            int64_t e = e2e[E * 3 + l];
+            if (PREC == EM_PREC_MIXED_COMP32) {
+                comp_add(nhi + 2 * e, nlo + 2 * e, (float)m[lo][0]);
+                comp_add(nhi + 2 * e + 1, nlo + 2 * e + 1, (float)m[lo][1]);
+            } else {
+                atomicAdd(n + 2 * e, m[lo][0]);
+                atomicAdd(n + 2 * e + 1, m[lo][1]);
+            }
+        }
+        if (vol || vhi) {
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                if (PREC == EM_PREC_MIXED_COMP32) comp_add(vhi + gid[i], vlo + gid[i], (float)vq);
+                else atomicAdd(vol + gid[i], vq);
+            }
+        }
+    }
+}
+
+__global__ void k_comp_finalize(int64_t m, const float* __restrict__ hi, const float* __restrict__ lo,
+                                double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = (double)hi[i] + (double)lo[i];
+}
+
+__device__ __forceinline__ int64_t find_bnode(const int32_t* bnode, int64_t nb, int32_t v) {
+    int64_t lo = 0, hi = nb - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int32_t t = bnode[mid];
+        if (t == v) return mid;
+        if (t < v) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// boundary faces: correction n_B/(D(D+1)) on the face's edges, n_B/D on its nodes
+template <int DIM>
+__global__ void k_bnd_atomic(int64_t nbf, const int32_t* __restrict__ bface, const int32_t* __restrict__ bowner,
+                             const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                             const double* __restrict__ x, int64_t nbn, const int32_t* __restrict__ bnode,
+                             double* __restrict__ n, double* __restrict__ bnormal) {
+    for (int64_t B = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; B < nbf; B += int64_t(gridDim.x) * blockDim.x) {
+        int32_t f = bowner[B];
+        int64_t E = f >> 2;
+        int o = f & 3;
+        if (DIM == 3) {
+            int p = bface[3 * B], q = bface[3 * B + 1], r = bface[3 * B + 2];
+            d3 xp = ld3(x, p);
+            d3 nB = 0.5 * cross(ld3(x, q) - xp, ld3(x, r) - xp);
+            if (n) {
+                d3 cB = (1.0 / 12.0) * nB;
+                for (int l = 0; l < 6; l++) {
+                    if (c_le3a[l][0] == o || c_le3a[l][1] == o) continue;
+                    int64_t e = e2e[E * 6 + l];
+                    atomicAdd(n + 3 * e, cB.x); atomicAdd(n + 3 * e + 1, cB.y); atomicAdd(n + 3 * e + 2, cB.z);
+                }
+            }
+            if (bnormal) {
+                d3 bB = (1.0 / 3.0) * nB;
+                int vv[3] = {p, q, r};
+                for (int i = 0; i < 3; i++) {
+                    int64_t k = find_bnode(bnode, nbn, vv[i]);
+                    atomicAdd(bnormal + 3 * k, bB.x); atomicAdd(bnormal + 3 * k + 1, bB.y); atomicAdd(bnormal + 3 * k + 2, bB.z);
+                }
+            }
+        } else {
+            int a = bface[2 * B], b2 = bface[2 * B + 1];
+            double nx = x[2 * int64_t(a) + 1] - x[2 * int64_t(b2) + 1], ny = x[2 * int64_t(b2)] - x[2 * int64_t(a)];
+            if (n) {
+                int l = (o == 0) ? 2 : (o == 1 ? 1 : 0);
+                int64_t e = e2e[E * 3 + l];
+                atomicAdd(n + 2 * e, nx / 6.0); atomicAdd(n + 2 * e + 1, ny / 6.0);
+            }
+            if (bnormal) {
+                int vv[2] = {a, b2};
+                for (int i = 0; i < 2; i++) {
+                    int64_t k = find_bnode(bnode, nbn, vv[i]);
+                    atomicAdd(bnormal + 2 * k, 0.5 * nx); atomicAdd(bnormal + 2 * k + 1, 0.5 * ny);
+                }
+            }
+        }
+    }
+}
+
+// ---- adjoint --------------------------------------------------------------
+template <int PREC>
+__global__ void k_adj_atomic3(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                              const double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ c,
+                              double* __restrict__ g) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        int4 v = reinterpret_cast<const int4*>(elems)[E];
+        int gid[4] = {v.x, v.y, v.z, v.w};
+        d3 W[4] = {mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0)};
+#pragma unroll
+        for (int l = 0; l < 6; l++) {
+            int p = c_le3a[l][0], q = c_le3a[l][1];
+            int lo = gid[p] < gid[q] ? p : q;
+            W[lo] = W[lo] + ld3(w, e2e[E * 6 + l]);
+        }
+        double C = c ? (c[gid[0]] + c[gid[1]] + c[gid[2]] + c[gid[3]]) : 0.0;
+        d3 p0 = ld3(x, gid[0]);
+        d3 a = ld3(x, gid[1]) - p0, b = ld3(x, gid[2]) - p0, cc = ld3(x, gid[3]) - p0;
+        d3 ga, gb, gc;
+        if (PREC == EM_PREC_FP64) {
+            d3 A1 = W[1] - W[0], A2 = W[2] - W[0], A3 = W[3] - W[0];
+            d3 N1 = cross(b, cc), N2 = cross(cc, a), N3 = cross(a, b);
+            double det = dot(a, N1);
+            double s = det > 0 ? 1.0 : -1.0;
+            double f = -s / 12.0, h = C * s / 24.0;
+            ga = f * (cross(A2, cc) - cross(A3, b)) + h * N1;
+            gb = f * (cross(A3, a) - cross(A1, cc)) + h * N2;
+            gc = f * (cross(A1, b) - cross(A2, a)) + h * N3;
+        } else {
+            f3 fa = tof(a), fb = tof(b), fc = tof(cc);
+            f3 A1 = tof(W[1] - W[0]), A2 = tof(W[2] - W[0]), A3 = tof(W[3] - W[0]);
+            f3 N1 = cross(fb, fc), N2 = cross(fc, fa), N3 = cross(fa, fb);
+            float det = dot(fa, N1);
+            float s = det > 0 ? 1.0f : -1.0f;
+            float f = -s / 12.0f, h = (float)C * s / 24.0f;
+            f3 qa = f * (cross(A2, fc) - cross(A3, fb)) + h * N1;
+            f3 qb = f * (cross(A3, fa) - cross(A1, fc)) + h * N2;
+            f3 qc = f * (cross(A1, fb) - cross(A2, fa)) + h * N3;
+            ga = mk(qa.x, qa.y, qa.z); gb = mk(qb.x, qb.y, qb.z); gc = mk(qc.x, qc.y, qc.z);
+        }
+        d3 g0 = -1.0 * (ga + gb + gc);
+        d3 gg[4] = {g0, ga, gb, gc};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            atomicAdd(g + 3 * int64_t(gid[i]), gg[i].x);
+            atomicAdd(g + 3 * int64_t(gid[i]) + 1, gg[i].y);
+            atomicAdd(g + 3 * int64_t(gid[i]) + 2, gg[i].z);
+        }
+    }
+}
+
+template <int PREC>
+__global__ void k_adj_atomic2(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                              const double* __restrict__ x, const double* __restrict__ w, const double* __restrict__ c,
+                              double* __restrict__ g) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        int4 v = reinterpret_cast<const int4*>(elems)[E];
+        int gid[3] = {v.x, v.y, v.z};
+        double W[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            int p = c_le2a[l][0], q = c_le2a[l][1];
+            int lo = gid[p] < gid[q] ? p : q;
+            int64_t e = e2e[E * 3 + l];
+            W[lo][0] += w[2 * e]; W[lo][1] += w[2 * e + 1];
+        }
+        double C = c ? (c[gid[0]] + c[gid[1]] + c[gid[2]]) : 0.0;
+        double ax = x[2 * int64_t(gid[1])] - x[2 * int64_t(gid[0])], ay = x[2 * int64_t(gid[1]) + 1] - x[2 * int64_t(gid[0]) + 1];
+        double bx = x[2 * int64_t(gid[2])] - x[2 * int64_t(gid[0])], by = x[2 * int64_t(gid[2]) + 1] - x[2 * int64_t(gid[0]) + 1];
+        double A1x = W[1][0] - W[0][0], A1y = W[1][1] - W[0][1], A2x = W[2][0] - W[0][0], A2y = W[2][1] - W[0][1];
+        double gax, gay, gbx, gby;
+        double det = ax * by - ay * bx;
+        double s = det > 0 ? 1.0 : -1.0;
+        double f = s / 3.0, h = C * s / 6.0;
+        gax = f * (-A2y) + h * by;  gay = f * A2x - h * bx;
+        gbx = f * A1y - h * ay;     gby = -f * A1x + h * ax;
+        if (PREC != EM_PREC_FP64) {
+            gax = (float)gax; gay = (float)gay; gbx = (float)gbx; gby = (float)gby;
+        }
+        double gg[3][2] = {{-(gax + gbx), -(gay + gby)}, {gax, gay}, {gbx, gby}};
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            atomicAdd(g + 2 * int64_t(gid[i]), gg[i][0]);
+            atomicAdd(g + 2 * int64_t(gid[i]) + 1, gg[i][1]);
+        }
+    }
+}
+
+template <int DIM>
+__global__ void k_bnd_adj_atomic(int64_t nbf, const int32_t* __restrict__ bface, const int32_t* __restrict__ bowner,
+                                 const int32_t* __restrict__ e2e, const double* __restrict__ x,
+                                 const double* __restrict__ w, double* __restrict__ g) {
+    for (int64_t B = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; B < nbf; B += int64_t(gridDim.x) * blockDim.x) {
+        int32_t f = bowner[B];
+        int64_t E = f >> 2;
+        int o = f & 3;
+        if (DIM == 3) {
+            d3 WB = mk(0, 0, 0);
+            for (int l = 0; l < 6; l++) {
+                if (c_le3a[l][0] == o || c_le3a[l][1] == o) continue;
+                WB = WB + ld3(w, e2e[E * 6 + l]);
+            }
+            int p = bface[3 * B], q = bface[3 * B + 1], r = bface[3 * B + 2];
+            d3 xp = ld3(x, p);
+            d3 u = ld3(x, q) - xp, t = ld3(x, r) - xp;
+            d3 gu = (1.0 / 24.0) * cross(t, WB), gt = (1.0 / 24.0) * cross(WB, u);
+            atomicAdd(g + 3 * int64_t(q), gu.x); atomicAdd(g + 3 * int64_t(q) + 1, gu.y); atomicAdd(g + 3 * int64_t(q) + 2, gu.z);
+            atomicAdd(g + 3 * int64_t(r), gt.x); atomicAdd(g + 3 * int64_t(r) + 1, gt.y); atomicAdd(g + 3 * int64_t(r) + 2, gt.z);
+            atomicAdd(g + 3 * int64_t(p), -(gu.x + gt.x));
+            atomicAdd(g + 3 * int64_t(p) + 1, -(gu.y + gt.y));
+            atomicAdd(g + 3 * int64_t(p) + 2, -(gu.z + gt.z));
+        } else {
+            int l = (o == 0) ? 2 : (o == 1 ? 1 : 0);
+            int64_t e = e2e[E * 3 + l];
+            int a = bface[2 * B], b2 = bface[2 * B + 1];
+            double gx = w[2 * e + 1] / 6.0, gy = -w[2 * e] / 6.0;   // d/d(x_b - x_a) of w.(-d_y, d_x)/6
+            atomicAdd(g + 2 * int64_t(b2), gx); atomicAdd(g + 2 * int64_t(b2) + 1, gy);
+            atomicAdd(g + 2 * int64_t(a), -gx); atomicAdd(g + 2 * int64_t(a) + 1, -gy);
+        }
+    }
+}
+
+}  // namespace
+
+size_t atomic_fwd_ws_bytes(const em_mesh* m, int prec) {
+    WsLayout L(nullptr);
+    if (prec == EM_PREC_MIXED_COMP32) {
+        L.take<float>(size_t(m->n_edges) * m->dim);
+        L.take<float>(size_t(m->n_edges) * m->dim);
+        L.take<float>(size_t(m->n_nodes));
+        L.take<float>(size_t(m->n_nodes));
+    }
+    return L.bytes();
+}
+
+int atomic_fwd(const em_mesh* m, int prec, const double* x, double* n, double* vol, double* bnormal, void* ws,
+               cudaStream_t s) {
+    const int T = 256;
+    const int dim = m->dim;
+    const unsigned G = grid_for(m->n_elems, T, int64_t(num_sms()) * 16);
+    float *nhi = nullptr, *nlo = nullptr, *vhi = nullptr, *vlo = nullptr;
+    if (prec == EM_PREC_MIXED_COMP32) {
+        WsLayout L(ws);
+        nhi = L.take<float>(size_t(m->n_edges) * dim);
+        nlo = L.take<float>(size_t(m->n_edges) * dim);
+        vhi = L.take<float>(size_t(m->n_nodes));
+        vlo = L.take<float>(size_t(m->n_nodes));
+        EM_CUDA_TRY(cudaMemsetAsync(nhi, 0, sizeof(float) * m->n_edges * dim, s));
+        EM_CUDA_TRY(cudaMemsetAsync(nlo, 0, sizeof(float) * m->n_edges * dim, s));
+        EM_CUDA_TRY(cudaMemsetAsync(vhi, 0, sizeof(float) * m->n_nodes, s));
+        EM_CUDA_TRY(cudaMemsetAsync(vlo, 0, sizeof(float) * m->n_nodes, s));
+    } else {
+        if (n) EM_CUDA_TRY(cudaMemsetAsync(n, 0, sizeof(double) * m->n_edges * dim, s));
+        if (vol) EM_CUDA_TRY(cudaMemsetAsync(vol, 0, sizeof(double) * m->n_nodes, s));
+    }
+    if (bnormal) EM_CUDA_TRY(cudaMemsetAsync(bnormal, 0, sizeof(double) * m->n_bnodes * dim, s));
+    double* vol_arg = (prec == EM_PREC_MIXED_COMP32) ? nullptr : vol;
+#define LAUNCH_FWD(K, P) K<P><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, n, vol_arg, nhi, nlo, vhi, vlo)
+    if (dim == 3) {
+        if (prec == EM_PREC_FP64) LAUNCH_FWD(k_fwd_atomic3, EM_PREC_FP64);
+        else if (prec == EM_PREC_MIXED) LAUNCH_FWD(k_fwd_atomic3, EM_PREC_MIXED);
+        else LAUNCH_FWD(k_fwd_atomic3, EM_PREC_MIXED_COMP32);
+    } else {
+        if (prec == EM_PREC_FP64) LAUNCH_FWD(k_fwd_atomic2, EM_PREC_FP64);
+        else if (prec == EM_PREC_MIXED) LAUNCH_FWD(k_fwd_atomic2, EM_PREC_MIXED);
+        else LAUNCH_FWD(k_fwd_atomic2, EM_PREC_MIXED_COMP32);
+    }
+#undef LAUNCH_FWD
+    note_launches(1);
+    EM_CUDA_TRY(cudaGetLastError());
+    if (prec == EM_PREC_MIXED_COMP32) {
+        k_comp_finalize<<<grid_for(m->n_edges * dim, T), T, 0, s>>>(m->n_edges * dim, nhi, nlo, n);
+        if (vol) k_comp_finalize<<<grid_for(m->n_nodes, T), T, 0, s>>>(m->n_nodes, vhi, vlo, vol);
+        note_launches(vol ? 2 : 1);
+    }
+    if (m->n_bfaces && (n || bnormal)) {
+        if (dim == 3)
+            k_bnd_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+        else
+            k_bnd_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+        note_launches(1);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+int atomic_adj(const em_mesh* m, int prec, const double* x, const double* w, const double* c, double* g,
+               cudaStream_t s) {
+    const int T = 256;
+    const int dim = m->dim;
+    const unsigned G = grid_for(m->n_elems, T, int64_t(num_sms()) * 16);
+    EM_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * m->n_nodes * dim, s));
+    if (dim == 3) {
+        if (prec == EM_PREC_FP64) k_adj_atomic3<EM_PREC_FP64><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, w, c, g);
+        else k_adj_atomic3<EM_PREC_MIXED><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, w, c, g);
+    } else {
+        if (prec == EM_PREC_FP64) k_adj_atomic2<EM_PREC_FP64><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, w, c, g);
+        else k_adj_atomic2<EM_PREC_MIXED><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, w, c, g);
+    }
+    note_launches(1);
+    if (m->n_bfaces) {
+        if (dim == 3)
+            k_bnd_adj_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
+                                                                      m->elem2edge, x, w, g);
+        else
+            k_bnd_adj_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
+                                                                      m->elem2edge, x, w, g);
+        note_launches(1);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+}  // namespace em

@@ -1,0 +1,43 @@
+// Internal entry points shared between the translation units of the library.
+#pragma once
+#include "em_common.cuh"
+
+namespace em {
+
+int edge_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const double* x, void* ws, size_t* ws_bytes,
+                    int32_t* edges, int64_t edges_cap, int32_t* elem2edge, int32_t* edge_ptr, int32_t* edge_slot,
+                    int32_t* bface, int32_t* bowner, int64_t bface_cap, int32_t* bnode, int64_t bnode_cap,
+                    int64_t* counts, cudaStream_t s);
+size_t check_elements_ws_bytes();
+int check_elements_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const double* x, void* ws,
+                        int64_t* counts, cudaStream_t s);
+
+size_t atomic_fwd_ws_bytes(const em_mesh* m, int prec);
+int atomic_fwd(const em_mesh* m, int prec, const double* x, double* n, double* vol, double* bnormal, void* ws,
+               cudaStream_t s);
+int atomic_adj(const em_mesh* m, int prec, const double* x, const double* w, const double* c, double* g,
+               cudaStream_t s);
+
+}  // namespace em
+
+namespace em {
+
+enum { GATHER_FWD = 1, GATHER_ADJ = 2 };
+
+size_t gather_ws_bytes(const em_mesh* m);
+int gather_run(const em_mesh* m, int prec, int what, const double* x, const double* w, const double* c, double* n,
+               double* vol, double* bnormal, double* g, void* ws, cudaStream_t s);
+
+size_t csr_fwd_ws_bytes(const em_mesh* m);
+int csr_fwd(const em_mesh* m, const double* x, double* n, double* vol, double* bnormal, void* ws, cudaStream_t s);
+
+int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const int32_t* elem2edge, int64_t n_edges,
+                    const int32_t* edges, int64_t nbf, const int32_t* bface, const int32_t* bowner, int64_t nbn,
+                    const int32_t* bnode, int tile_nodes, void* ws, size_t* ws_bytes, void* plan, size_t* plan_bytes,
+                    cudaStream_t s);
+int plan_tiles_impl(const void* plan, int64_t* n_tiles, cudaStream_t s);
+
+int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int precision, int blocks,
+                 int32_t* status, void* ws, size_t* ws_bytes, cudaStream_t s);
+
+}  // namespace em
