@@ -28,7 +28,6 @@ namespace {
 __constant__ int c_le3a[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 __constant__ int c_le2a[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 
-__device__ __forceinline__ int vcomp(const int4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
 struct d3 { double x, y, z; };
 __device__ __forceinline__ d3 mk(double a, double b, double c) { return {a, b, c}; }
@@ -209,6 +208,7 @@ __global__ void k_bnd_atomic(int64_t nbf, const int32_t* __restrict__ bface, con
                 int vv[3] = {p, q, r};
                 for (int i = 0; i < 3; i++) {
                     int64_t k = find_bnode(bnode, nbn, vv[i]);
+                    if (k < 0) continue;
                     atomicAdd(bnormal + 3 * k, bB.x); atomicAdd(bnormal + 3 * k + 1, bB.y); atomicAdd(bnormal + 3 * k + 2, bB.z);
                 }
             }
@@ -224,6 +224,7 @@ __global__ void k_bnd_atomic(int64_t nbf, const int32_t* __restrict__ bface, con
                 int vv[2] = {a, b2};
                 for (int i = 0; i < 2; i++) {
                     int64_t k = find_bnode(bnode, nbn, vv[i]);
+                    if (k < 0) continue;
                     atomicAdd(bnormal + 2 * k, 0.5 * nx); atomicAdd(bnormal + 2 * k + 1, 0.5 * ny);
                 }
             }
