@@ -14,6 +14,6 @@ def __getattr__(name):
     # import the torch-based binding lazily so the C-ABI symbol checks run
     # without importing torch
     if name == "api":
-        from . import api
-        return api
+        import importlib
+        return importlib.import_module(__name__ + ".api")
     raise AttributeError(name)

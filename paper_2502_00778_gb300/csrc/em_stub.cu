@@ -9,10 +9,6 @@ size_t csr_fwd_ws_bytes(const em_mesh*) { return 0; }
 int csr_fwd(const em_mesh*, const double*, double*, double*, double*, void*, cudaStream_t) {
     return fail(EM_ERR_ARG, "CSR path not available");
 }
-int plan_build_impl(int, int64_t, int64_t, const int32_t*, const int32_t*, int64_t, const int32_t*, int64_t,
-                    const int32_t*, const int32_t*, int64_t, const int32_t*, int, void*, size_t*, void*, size_t*,
-                    cudaStream_t) { return fail(EM_ERR_ARG, "plan not available"); }
-int plan_tiles_impl(const void*, int64_t*, cudaStream_t) { return fail(EM_ERR_ARG, "plan not available"); }
 int batched_impl(int, const em_batch_item*, const int64_t*, int, int, int32_t*, void*, size_t*, cudaStream_t) {
     return fail(EM_ERR_ARG, "batched path not available");
 }
