@@ -144,6 +144,19 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
                   int64_t* counts,
                   void* stream);
 
+/* host summary of a plan (em_plan_build's plan_info output, em_mesh.plan_info) */
+#define EM_PLAN_INFO_LEN 12
+#define EM_PLAN_INFO_TILE_NODES 0   /* nodes per tile */
+#define EM_PLAN_INFO_TILES      1   /* number of tiles */
+#define EM_PLAN_INFO_MAX_ELEMS  2   /* most elements in one tile */
+#define EM_PLAN_INFO_MAX_NODES  3   /* most nodes (owned + halo) in one tile */
+#define EM_PLAN_INFO_MAX_EDGES  4   /* most edges (owned + halo) in one tile */
+#define EM_PLAN_INFO_MAX_OWNED_EDGES 5
+#define EM_PLAN_INFO_MAX_BFACES 6
+#define EM_PLAN_INFO_MAX_OWNED_BNODES 7
+#define EM_PLAN_INFO_MAX_OWNED_NODES 8
+#define EM_PLAN_INFO_CHECK      9   /* plan size in bytes, echoed for validation */
+
 /* em_plan_build -- tiled gather plan for EM_PATH_GATHER (run once per
  * connectivity, after em_edge_build).
  *
@@ -156,9 +169,18 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
  *   plan         device buffer of *plan_bytes bytes, written; call with
  *                plan == NULL to query the size (an upper bound from the
  *                counts; the bound needs no device work).
- *   tile_nodes   nodes per tile, 32..2048, multiple of 32 (0 = default 512).
- * The plan stores device pointers to nothing: it is position-independent and
- * may be copied.  Synchronizes `stream`. */
+ *   tile_nodes   nodes per tile, 32..2048, multiple of 32 (0 = default 256).
+ *   plan_info    HOST int64[EM_PLAN_INFO_LEN] or NULL, written on success:
+ *                the summary to copy into em_mesh.plan_info.
+ * Protocol (three calls, all synchronizing `stream`):
+ *   1. ws == NULL            -> *ws_bytes = scratch for step 2;
+ *   2. ws given, plan NULL   -> counts; *plan_bytes = exact plan size and
+ *                               *ws_bytes = scratch for step 3;
+ *   3. ws and plan given     -> builds the plan.
+ * Errors: EM_ERR_ARG (bad sizes, a tile exceeding the 16-bit local index
+ * limits: choose a smaller tile_nodes), EM_ERR_WORKSPACE, EM_ERR_CUDA.
+ * The plan holds no device pointers: it is position-independent and may be
+ * copied. */
 int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems,
                   const int32_t* elem2edge,
                   int64_t n_edges, const int32_t* edges,
@@ -167,6 +189,7 @@ int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elem
                   int tile_nodes,
                   void* ws, size_t* ws_bytes,
                   void* plan, size_t* plan_bytes,
+                  int64_t* plan_info,
                   void* stream);
 
 /* ------------------------------------------------------------------------ */
@@ -188,6 +211,9 @@ typedef struct em_mesh {
     const int32_t* bnode;        /* [n_bnodes] */
     const void* plan;            /* from em_plan_build, needed by EM_PATH_GATHER only */
     size_t plan_bytes;
+    int64_t plan_info[EM_PLAN_INFO_LEN]; /* host copy of the plan summary written by
+                                    em_plan_build (GATHER path only); lets launches size
+                                    their shared memory without reading the device */
 } em_mesh;
 
 /* em_edge_metrics -- forward: n_edge [n_edges][dim], vol [n_nodes],

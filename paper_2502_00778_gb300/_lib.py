@@ -32,6 +32,7 @@ class EmMesh(_c.Structure):
         ("elems", _vp), ("elem2edge", _vp), ("edges", _vp), ("edge_ptr", _vp), ("edge_slot", _vp),
         ("bface", _vp), ("bface_owner", _vp), ("bnode", _vp),
         ("plan", _vp), ("plan_bytes", _c.c_size_t),
+        ("plan_info", _c.c_int64 * 12),
     ]
 
 
@@ -50,7 +51,7 @@ SIGNATURES = {
     "em_edge_build": ([_c.c_int, _i64, _i64, _vp, _vp, _vp, _szp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64,
                        _i64p, _vp], _c.c_int),
     "em_plan_build": ([_c.c_int, _i64, _i64, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _c.c_int, _vp, _szp,
-                       _vp, _szp, _vp], _c.c_int),
+                       _vp, _szp, _i64p, _vp], _c.c_int),
     "em_edge_metrics": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _szp, _vp], _c.c_int),
     "em_edge_metrics_adjoint": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _szp, _vp],
                                 _c.c_int),

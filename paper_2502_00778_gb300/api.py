@@ -64,6 +64,7 @@ class Topology:
         self.bface_owner = bface_owner
         self.bnode = bnode
         self.plan = None
+        self.plan_info = None
         self.tile_nodes = None
 
     @property
@@ -97,6 +98,9 @@ class Topology:
         m.bnode = self.bnode.data_ptr() if self.n_bnodes else None
         m.plan = self.plan.data_ptr() if self.plan is not None else None
         m.plan_bytes = self.plan.numel() if self.plan is not None else 0
+        if self.plan_info is not None:
+            for i, v in enumerate(self.plan_info):
+                m.plan_info[i] = v
         return m
 
 
@@ -145,12 +149,17 @@ def plan_build(topo: Topology, tile_nodes: int = 0) -> Topology:
             _ptr(topo.edges), topo.n_bfaces, _ptr(topo.bface) if topo.n_bfaces else null,
             _ptr(topo.bface_owner) if topo.n_bfaces else null, topo.n_bnodes,
             _ptr(topo.bnode) if topo.n_bnodes else null, int(tile_nodes))
-    check(L.em_plan_build(*args, null, ctypes.byref(wsb), null, ctypes.byref(pb), _stream()))
+    info = (ctypes.c_int64 * 12)()
+    # 1: scratch for the count pass; 2: exact plan and scratch sizes; 3: build
+    check(L.em_plan_build(*args, null, ctypes.byref(wsb), null, ctypes.byref(pb), info, _stream()))
+    ws = workspace.get(wsb.value, dev)
+    check(L.em_plan_build(*args, _ptr(ws), ctypes.byref(wsb), null, ctypes.byref(pb), info, _stream()))
     ws = workspace.get(wsb.value, dev)
     plan = torch.empty(max(pb.value, 256), dtype=torch.uint8, device=dev)
-    check(L.em_plan_build(*args, _ptr(ws), ctypes.byref(wsb), _ptr(plan), ctypes.byref(pb), _stream()))
-    topo.plan = plan[:pb.value] if pb.value <= plan.numel() else plan
-    topo.tile_nodes = tile_nodes
+    check(L.em_plan_build(*args, _ptr(ws), ctypes.byref(wsb), _ptr(plan), ctypes.byref(pb), info, _stream()))
+    topo.plan = plan
+    topo.plan_info = list(info)
+    topo.tile_nodes = info[0]
     return topo
 
 

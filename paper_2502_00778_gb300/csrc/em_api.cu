@@ -169,9 +169,10 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, const double* x, c
 int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems, const int32_t* elem2edge,
                   int64_t n_edges, const int32_t* edges, int64_t n_bfaces, const int32_t* bface,
                   const int32_t* bface_owner, int64_t n_bnodes, const int32_t* bnode, int tile_nodes, void* ws,
-                  size_t* ws_bytes, void* plan, size_t* plan_bytes, void* stream) {
+                  size_t* ws_bytes, void* plan, size_t* plan_bytes, int64_t* plan_info, void* stream) {
     int st = plan_build_impl(dim, n_nodes, n_elems, elems, elem2edge, n_edges, edges, n_bfaces, bface, bface_owner,
-                             n_bnodes, bnode, tile_nodes, ws, ws_bytes, plan, plan_bytes, as_stream(stream));
+                             n_bnodes, bnode, tile_nodes, ws, ws_bytes, plan, plan_bytes, plan_info,
+                             as_stream(stream));
     return st == EM_OK ? ok() : st;
 }
 

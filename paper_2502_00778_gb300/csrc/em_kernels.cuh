@@ -34,7 +34,7 @@ int csr_fwd(const em_mesh* m, const double* x, double* n, double* vol, double* b
 int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const int32_t* elem2edge, int64_t n_edges,
                     const int32_t* edges, int64_t nbf, const int32_t* bface, const int32_t* bowner, int64_t nbn,
                     const int32_t* bnode, int tile_nodes, void* ws, size_t* ws_bytes, void* plan, size_t* plan_bytes,
-                    cudaStream_t s);
+                    int64_t* plan_info, cudaStream_t s);
 int plan_tiles_impl(const void* plan, int64_t* n_tiles, cudaStream_t s);
 
 int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int precision, int blocks,

@@ -431,7 +431,7 @@ int csr_from_keys(uint64_t* keys, int64_t n, int64_t nkeys, int32_t* cnt, int64_
 int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const int32_t* e2e, int64_t n_edges,
                     const int32_t* edges, int64_t nbf, const int32_t* bface, const int32_t* bowner, int64_t nbn,
                     const int32_t* bnode, int tile_nodes, void* ws, size_t* ws_bytes, void* plan, size_t* plan_bytes,
-                    cudaStream_t s) {
+                    int64_t* plan_info, cudaStream_t s) {
     if (dim != 2 && dim != 3) return fail(EM_ERR_ARG, "dim must be 2 or 3");
     if (nv <= 0 || ne <= 0 || n_edges <= 0 || nbf < 0 || nbn < 0) return fail(EM_ERR_ARG, "bad sizes");
     if (!ws_bytes || !plan_bytes) return fail(EM_ERR_ARG, "ws_bytes and plan_bytes must not be NULL");
@@ -664,6 +664,19 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     EM_CUDA_TRY(cudaMemcpyAsync(plan, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     EM_CUDA_TRY(cudaStreamSynchronize(s));
     *plan_bytes = (size_t)po.total;
+    if (plan_info) {
+        for (int i = 0; i < EM_PLAN_INFO_LEN; i++) plan_info[i] = 0;
+        plan_info[EM_PLAN_INFO_TILE_NODES] = T;
+        plan_info[EM_PLAN_INFO_TILES] = n_tiles;
+        plan_info[EM_PLAN_INFO_MAX_ELEMS] = h.max_el;
+        plan_info[EM_PLAN_INFO_MAX_NODES] = h.max_nodes;
+        plan_info[EM_PLAN_INFO_MAX_EDGES] = h.max_edges;
+        plan_info[EM_PLAN_INFO_MAX_OWNED_EDGES] = h.max_eo;
+        plan_info[EM_PLAN_INFO_MAX_BFACES] = h.max_bf;
+        plan_info[EM_PLAN_INFO_MAX_OWNED_BNODES] = h.max_bo;
+        plan_info[EM_PLAN_INFO_MAX_OWNED_NODES] = h.max_own;
+        plan_info[EM_PLAN_INFO_CHECK] = po.total;
+    }
     return EM_OK;
 }
 

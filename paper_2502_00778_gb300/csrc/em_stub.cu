@@ -2,9 +2,6 @@
 #include "em_common.cuh"
 #include "em_kernels.cuh"
 namespace em {
-size_t gather_ws_bytes(const em_mesh*) { return 0; }
-int gather_run(const em_mesh*, int, int, const double*, const double*, const double*, double*, double*, double*,
-               double*, void*, cudaStream_t) { return fail(EM_ERR_ARG, "gather path not available"); }
 size_t csr_fwd_ws_bytes(const em_mesh*) { return 0; }
 int csr_fwd(const em_mesh*, const double*, double*, double*, double*, void*, cudaStream_t) {
     return fail(EM_ERR_ARG, "CSR path not available");
