@@ -239,21 +239,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     edge_build_ms = (time.perf_counter() - t0) * 1e3
     del topo2
-    have_gather = True
-    try:
-        t0 = time.perf_counter()
-        api.plan_build(topo, args.tile_nodes)
-        torch.cuda.synchronize()
-        plan_build_ms = (time.perf_counter() - t0) * 1e3
-    except Exception:
-        have_gather = False
-        plan_build_ms = None
-    path = args.path or ("gather" if have_gather else "atomic")
+    path = args.path or "gather"
     prec = args.prec or ("dw" if path == "gather" else "fp64")
-
     g = torch.Generator(device="cpu").manual_seed(meshgen.SEED_BASE + 5)
     w = torch.randn((topo.n_edges, m.dim), generator=g, dtype=torch.float64).to(dev)
     c = torch.randn(m.n_nodes, generator=g, dtype=torch.float64).to(dev)
+    have_gather = True
+    sweep = None
+    try:
+        if args.tile_nodes:
+            tile = args.tile_nodes
+        else:
+            from paper_2502_00778_gb300 import autotune
+            tile, sweep = autotune.tune(topo, x, w, c, "fused", prec if path == "gather" else "dw", use_cache=False)
+        t0 = time.perf_counter()
+        api.plan_build(topo, tile)
+        torch.cuda.synchronize()
+        plan_build_ms = (time.perf_counter() - t0) * 1e3
+    except Exception as ex:
+        print(f"gather path unavailable: {ex}", file=sys.stderr)
+        have_gather = False
+        plan_build_ms = None
+        tile = None
+        if path == "gather":
+            path, prec = "atomic", "fp64"
     outs = (torch.empty((topo.n_edges, m.dim), dtype=torch.float64, device=dev),
             torch.empty(m.n_nodes, dtype=torch.float64, device=dev),
             torch.empty((topo.n_bnodes, m.dim), dtype=torch.float64, device=dev),
@@ -364,7 +373,7 @@ def run_ours(args):
     # ---- per-form comparison (same workload, separate short timings) ----
     forms = {}
     if not args.no_forms and rank == 0:
-        cand = [("atomic", "fp64"), ("atomic", "mixed")]
+        cand = [("atomic", "fp64"), ("atomic", "mixed"), ("csr", "fp64")]
         if have_gather:
             cand += [("gather", "fp64"), ("gather", "dw"), ("gather", "mixed")]
         for pth, pr in cand:
@@ -372,6 +381,9 @@ def run_ours(args):
                 def fstep():
                     if pth == "gather":
                         api.edge_metrics_fused(topo, x, w, c, pr, out=outs)
+                    elif pth == "csr":
+                        api.edge_metrics(topo, x, pr, "csr", out=outs[:3])
+                        api.edge_metrics_adjoint(topo, x, w, c, pr, "atomic", out=outs[3])
                     else:
                         api.edge_metrics(topo, x, pr, pth, out=outs[:3])
                         api.edge_metrics_adjoint(topo, x, w, c, pr, pth, out=outs[3])
@@ -407,7 +419,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "elements": m.n_elems, "nodes": m.n_nodes, "edges": topo.n_edges,
                        "path": path, "precision": prec, "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (no flush needed)", "tile_nodes": args.tile_nodes},
+                       "l2": "inputs larger than L2 (no flush needed)", "tile_nodes": tile,
+                       "tile_sweep_ms": sweep},
             "hbm_gbs_step": step_bytes / (ms_per_step * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kname,

@@ -1,0 +1,96 @@
+"""Tile-size autotuner for the tiled gather path.
+
+The tile size (nodes per tile) sets the partition of the grid: larger tiles
+recompute fewer halo elements but need more shared memory per block, so fewer
+blocks are resident per SM.  `tune()` builds a plan for each candidate size,
+times the requested pass with CUDA events and keeps the fastest; results are
+cached in a JSON file keyed by the grid, the pass, the arithmetic form and the
+GPU, so later runs reuse the choice.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import api
+from ._lib import EMError
+
+CANDIDATES = (64, 96, 128, 160, 192, 256)
+
+
+def _cache_path():
+    return os.environ.get("EM_AUTOTUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "edgemetrics",
+                                                               "autotune.json")
+
+
+def _key(topo, what, precision):
+    dev = torch.cuda.get_device_name()
+    return f"{dev}|dim{topo.dim}|v{topo.n_nodes}|e{topo.n_elems}|{what}|{precision}"
+
+
+def _load():
+    p = _cache_path()
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d):
+    p = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + f".{os.getpid()}"
+        json.dump(d, open(tmp, "w"), indent=1)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def _time(fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune(topo, x, w=None, c=None, what="fused", precision="dw", candidates=CANDIDATES, reps=5, use_cache=True):
+    """Pick tile_nodes for `what` in {"fwd", "adj", "fused"}; builds the
+    winning plan into topo and returns (tile_nodes, {tile: ms or error})."""
+    cache = _load() if use_cache else {}
+    key = _key(topo, what, precision)
+    if use_cache and key in cache:
+        t = int(cache[key]["tile_nodes"])
+        api.plan_build(topo, t)
+        return t, cache[key].get("sweep", {})
+    sweep = {}
+    best = None
+    for t in candidates:
+        try:
+            api.plan_build(topo, t)
+            if what == "fwd":
+                fn = lambda: api.edge_metrics(topo, x, precision, "gather")  # noqa: E731
+            elif what == "adj":
+                fn = lambda: api.edge_metrics_adjoint(topo, x, w, c, precision, "gather")  # noqa: E731
+            else:
+                fn = lambda: api.edge_metrics_fused(topo, x, w, c, precision)  # noqa: E731
+            ms = _time(fn, reps)
+            sweep[str(t)] = round(ms, 4)
+            if best is None or ms < best[1]:
+                best = (t, ms)
+        except EMError as ex:
+            sweep[str(t)] = f"unusable: {str(ex)[:80]}"
+    if best is None:
+        raise EMError(-1, f"no usable tile size among {candidates}")
+    api.plan_build(topo, best[0])
+    cache[key] = {"tile_nodes": best[0], "ms": best[1], "sweep": sweep}
+    if use_cache:
+        _store(cache)
+    return best[0], sweep
