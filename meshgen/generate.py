@@ -310,3 +310,34 @@ def cached_workload(name: str, cache_dir: str = None, **override) -> Mesh:
     np.savez(tmp, x=m.x, elems=m.elems, dim=m.dim, h=m.h, meta=json.dumps(m.meta))
     os.replace(tmp, path)
     return m
+
+
+# ----------------------------------------------------------------------------
+# counter-based loss weights: w(j,k) and c(v) as functions of node ids
+# (SplitMix64, Steele, Lea & Flood, OOPSLA 2014), so that a checker can
+# evaluate them without the edge numbering
+# ----------------------------------------------------------------------------
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _splitmix64(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def _u11(z: np.ndarray) -> np.ndarray:
+    return (_splitmix64(z) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0) * 2.0 - 1.0
+
+
+def hash_weights(edges: np.ndarray, n_nodes: int, dim: int, seed: int):
+    """w[e] = U[-1,1)^dim from the key (j << 32 | k); c[v] = U[-1,1) from v."""
+    s = np.uint64(seed)
+    key = (edges[:, 0].astype(np.uint64) << np.uint64(32)) | edges[:, 1].astype(np.uint64)
+    with np.errstate(over="ignore"):
+        w = np.stack([_u11(s ^ (key * np.uint64(4) + np.uint64(c))) for c in range(dim)], axis=1)
+        v = np.arange(n_nodes, dtype=np.uint64)
+        c = _u11(s ^ ((v << np.uint64(2)) | np.uint64(3)) ^ np.uint64(0x5BD1E995))
+    return w, c

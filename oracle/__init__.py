@@ -58,6 +58,9 @@ def lib():
             L.or_fd_gradient.restype = None
             L.or_fd_gradient.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i32p, _i64, _i32p, _i64, _i32p,
                                          _f64p, _f64p, _i64, _i64p, ctypes.c_double, _f64p]
+            L.or_sample.restype = None
+            L.or_sample.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i64, _i32p, _i32p, _f64p, _i64, _i32p,
+                                    _f64p, _f64p, ctypes.c_uint64, _f64p]
             _lib = L
     return _lib
 
@@ -208,3 +211,22 @@ def fd_gradient(dim, x, elems, topo, w, c, nodes, delta):
                          topo.n_edges, _p(topo.edges, _i32p), topo.bface.shape[0], _p(topo.bface, _i32p),
                          _p(w, _f64p), _p(c, _f64p), nodes.shape[0], _p(nodes, _i64p), float(delta), _p(g, _f64p))
     return g
+
+
+def sample(dim, x, elems, edge_j, edge_k, nodes, seed):
+    """n at the sampled edges (j<k), and V, bnormal, dL/dx at the sampled
+    nodes, each computed from the elements around it; L uses the counter-based
+    weights w(j,k), c(v) (SplitMix64 of the node ids, see or_hash_w)."""
+    x = _c(x, np.float64)
+    elems = _c(elems, np.int32)
+    ej = _c(edge_j, np.int32)
+    ek = _c(edge_k, np.int32)
+    nd = _c(nodes, np.int32)
+    n = np.empty((ej.shape[0], dim))
+    v = np.empty(nd.shape[0])
+    b = np.empty((nd.shape[0], dim))
+    g = np.empty((nd.shape[0], dim))
+    lib().or_sample(dim, x.shape[0], _p(x, _f64p), elems.shape[0], _p(elems, _i32p), ej.shape[0], _p(ej, _i32p),
+                    _p(ek, _i32p), _p(n, _f64p), nd.shape[0], _p(nd, _i32p), _p(v, _f64p), _p(b, _f64p),
+                    ctypes.c_uint64(seed), _p(g, _f64p))
+    return n, v, b, g

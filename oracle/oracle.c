@@ -568,3 +568,205 @@ void or_fd_gradient(int dim, int64_t nv, double* x, int64_t ne, const int32_t* e
     }
     free(pos); free(ecnt); free(bcnt); free(elist); free(blist); free(efill); free(bfill);
 }
+
+/* ------------------------------------------------------------------------ */
+/* sampled evaluation (one output at a time, from the elements around it)  */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the counter-based generator used to define the
+ * loss weights of the sampled checks, w(j,k) and c(v), as a function of the
+ * edge's end nodes / the node id, so no edge numbering is needed. */
+static uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+/* uniform in [-1, 1): 53 random bits */
+static double u11(uint64_t z) { return (double)(splitmix64(z) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; }
+
+void or_hash_w(int dim, int32_t j, int32_t k, uint64_t seed, double* w) {
+    uint64_t key = ((uint64_t)(uint32_t)j << 32) | (uint32_t)k;
+    for (int c = 0; c < dim; c++) w[c] = u11(seed ^ (key * 4u + (uint64_t)c));
+}
+double or_hash_c(int32_t v, uint64_t seed) { return u11(seed ^ (((uint64_t)(uint32_t)v << 2) | 3u) ^ 0x5bd1e995ULL); }
+
+/* elements containing each marked node: CSR over the marked nodes */
+typedef struct { int64_t* ptr; int64_t* list; int64_t* pos; } nodestar;
+
+static nodestar build_stars(int dim, int64_t nv, int64_t ne, const int32_t* elems, int64_t nn, const int32_t* nodes) {
+    nodestar s;
+    s.pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)nv);
+    for (int64_t v = 0; v < nv; v++) s.pos[v] = -1;
+    for (int64_t i = 0; i < nn; i++) s.pos[nodes[i]] = i;
+    s.ptr = (int64_t*)calloc((size_t)nn + 1, sizeof(int64_t));
+    for (int64_t E = 0; E < ne; E++)
+        for (int i = 0; i < dim + 1; i++) { int64_t p = s.pos[elems[4 * E + i]]; if (p >= 0) s.ptr[p + 1]++; }
+    for (int64_t i = 0; i < nn; i++) s.ptr[i + 1] += s.ptr[i];
+    s.list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s.ptr[nn] + 1));
+    int64_t* fill = (int64_t*)calloc((size_t)nn + 1, sizeof(int64_t));
+    for (int64_t E = 0; E < ne; E++)
+        for (int i = 0; i < dim + 1; i++) { int64_t p = s.pos[elems[4 * E + i]]; if (p >= 0) s.list[s.ptr[p] + fill[p]++] = E; }
+    free(fill);
+    return s;
+}
+static void free_stars(nodestar* s) { free(s->ptr); free(s->list); free(s->pos); }
+
+static int elem_has(int dim, const int32_t* el, int32_t v) { for (int i = 0; i < dim + 1; i++) if (el[i] == v) return 1; return 0; }
+
+/* faces of the star of node j that contain j and are seen by exactly one star
+ * element: the boundary faces through j.  Calls fn for each, with the face's
+ * nodes in outward order (the stored order of the boundary face list). */
+static int face_key_eq(const int32_t* a, const int32_t* b, int n) { for (int i = 0; i < n; i++) if (a[i] != b[i]) return 0; return 1; }
+
+static int64_t star_bfaces(int dim, const double* x, const int32_t* elems, const int64_t* star, int64_t ns, int32_t j,
+                           int32_t* out /* [cap][dim] outward order */, int64_t cap) {
+    int64_t nb = 0;
+    for (int64_t a = 0; a < ns; a++) {
+        const int32_t* el = elems + 4 * star[a];
+        for (int o = 0; o < dim + 1; o++) {
+            if (el[o] == j) continue;                 /* faces through j only */
+            int32_t f[3] = {0, 0, 0}; int c = 0;
+            for (int i = 0; i < dim + 1; i++) if (i != o) f[c++] = el[i];
+            isort(f, dim);
+            int count = 0;
+            for (int64_t b = 0; b < ns; b++) {
+                const int32_t* eb = elems + 4 * star[b];
+                int all = 1;
+                for (int i = 0; i < dim; i++) all &= elem_has(dim, eb, f[i]);
+                count += all;
+            }
+            if (count != 1) continue;
+            /* orient outward exactly as or_bfaces does */
+            double nB[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+            face_area_vector(dim, x, f, nB);
+            for (int q = 0; q < dim; q++) d[q] = x[dim * el[o] + q] - x[dim * f[0] + q];
+            if (dot(nB, d, dim) > 0) {
+                if (dim == 3) { int32_t t = f[1]; f[1] = f[2]; f[2] = t; }
+                else { int32_t t = f[0]; f[0] = f[1]; f[1] = t; }
+            }
+            if (nb < cap) for (int q = 0; q < dim; q++) out[nb * dim + q] = f[q];
+            nb++;
+        }
+    }
+    return nb;
+}
+
+/* n at sampled edges (sj < sk), V and bnormal at sampled nodes, gradient of
+ * L (with w(j,k), c(v) from or_hash_w / or_hash_c) at sampled nodes; every
+ * value is computed from the elements around its edge or node with the same
+ * formulas as or_direct / or_adjoint. */
+void or_sample(int dim, int64_t nv, const double* x, int64_t ne, const int32_t* elems,
+               int64_t nse, const int32_t* sj, const int32_t* sk, double* n_out,
+               int64_t nsn, const int32_t* sn, double* v_out, double* b_out, uint64_t seed, double* g_out) {
+    const int nl = nloc_edges(dim);
+    const int (*le)[2] = local_edges(dim);
+    int64_t nq = nse + nsn;
+    int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nq > 0 ? nq : 1));
+    for (int64_t i = 0; i < nse; i++) nodes[i] = sj[i];
+    for (int64_t i = 0; i < nsn; i++) nodes[nse + i] = sn[i];
+    /* de-duplicate the marked set through pos[] (last index wins) */
+    nodestar st = build_stars(dim, nv, ne, elems, nq, nodes);
+    int32_t fb[64 * 3];
+    for (int64_t s = 0; s < nse; s++) {
+        int32_t j = sj[s], k = sk[s];
+        int64_t p = st.pos[j];
+        const int64_t* star = st.list + st.ptr[p];
+        int64_t ns = st.ptr[p + 1] - st.ptr[p];
+        double acc[3] = {0, 0, 0};
+        for (int64_t a = 0; a < ns; a++) {
+            const int32_t* el = elems + 4 * star[a];
+            if (!elem_has(dim, el, k)) continue;
+            for (int l = 0; l < nl; l++) {
+                int32_t u = el[le[l][0]], w2 = el[le[l][1]];
+                if (!((u == j && w2 == k) || (u == k && w2 == j))) continue;
+                double nj[3] = {0, 0, 0};
+                face_opposite(dim, x, el, low_end(el, le[l]), nj);
+                for (int c = 0; c < dim; c++) acc[c] += (dim == 3) ? 2.0 * nj[c] : nj[c] / 3.0;
+            }
+        }
+        int64_t nb = star_bfaces(dim, x, elems, star, ns, j, fb, 64);
+        for (int64_t b = 0; b < nb && b < 64; b++) {
+            const int32_t* f = fb + dim * b;
+            int hasj = 0, hask = 0;
+            for (int q = 0; q < dim; q++) { hasj |= f[q] == j; hask |= f[q] == k; }
+            if (!(hasj && hask)) continue;
+            double nB[3] = {0, 0, 0};
+            face_area_vector(dim, x, f, nB);
+            for (int c = 0; c < dim; c++) acc[c] += (dim == 3) ? nB[c] : nB[c] / 6.0;
+        }
+        for (int c = 0; c < dim; c++) n_out[dim * s + c] = (dim == 3) ? acc[c] * (1.0 / 12.0) : acc[c];
+    }
+    for (int64_t s = 0; s < nsn; s++) {
+        int32_t v = sn[s];
+        int64_t p = st.pos[v];
+        const int64_t* star = st.list + st.ptr[p];
+        int64_t ns = st.ptr[p + 1] - st.ptr[p];
+        double vol = 0, bn[3] = {0, 0, 0};
+        double* g = g_out + dim * s;
+        double gg[3] = {0, 0, 0};
+        for (int64_t a = 0; a < ns; a++) {
+            const int32_t* el = elems + 4 * star[a];
+            vol += elem_volume(dim, x, el) / (double)(dim + 1);
+            /* gradient of this element's share of L, read at node v: build a
+             * local gradient over the element's nodes with or_adjoint's rules */
+            double wl[6][3];
+            int32_t e2e_local[6];
+            for (int l = 0; l < nl; l++) {
+                int32_t a0 = el[le[l][0]], a1 = el[le[l][1]];
+                or_hash_w(dim, a0 < a1 ? a0 : a1, a0 < a1 ? a1 : a0, seed, wl[l]);
+                e2e_local[l] = l;
+            }
+            double cl[4];
+            for (int i = 0; i < dim + 1; i++) cl[i] = or_hash_c(el[i], seed);
+            /* local copies indexed 0..dim with node ids 0..dim */
+            double xl[12];
+            int32_t ell[4] = {0, 1, 2, dim == 3 ? 3 : -1};
+            for (int i = 0; i < dim + 1; i++) for (int q = 0; q < dim; q++) xl[dim * i + q] = x[dim * el[i] + q];
+            /* lower-end choice must follow the GLOBAL ids: reorder the local
+             * copy so that local order equals global order */
+            int ord[4] = {0, 1, 2, 3};
+            for (int i2 = 1; i2 < dim + 1; i2++) { int t = ord[i2], q2 = i2 - 1; while (q2 >= 0 && el[ord[q2]] > el[t]) { ord[q2 + 1] = ord[q2]; q2--; } ord[q2 + 1] = t; }
+            double xs[12]; double cs[4]; int32_t gid[4];
+            for (int i = 0; i < dim + 1; i++) { gid[i] = el[ord[i]]; cs[i] = cl[ord[i]]; for (int q = 0; q < dim; q++) xs[dim * i + q] = xl[dim * ord[i] + q]; }
+            double ws[6][3];
+            for (int l = 0; l < nl; l++) {
+                int32_t a0 = gid[le[l][0]], a1 = gid[le[l][1]];
+                or_hash_w(dim, a0 < a1 ? a0 : a1, a0 < a1 ? a1 : a0, seed, ws[l]);
+            }
+            double glocal[12] = {0};
+            double wflat[18];
+            for (int l = 0; l < nl; l++) for (int q = 0; q < dim; q++) wflat[dim * l + q] = ws[l][q];
+            elem_grad(dim, xs, ell, e2e_local, wflat, cs, glocal);
+            int iv = -1;
+            for (int i = 0; i < dim + 1; i++) if (gid[i] == v) iv = i;
+            for (int q = 0; q < dim; q++) gg[q] += glocal[dim * iv + q];
+            (void)wl;
+        }
+        int64_t nb = star_bfaces(dim, x, elems, star, ns, v, fb, 64);
+        for (int64_t b = 0; b < nb && b < 64; b++) {
+            const int32_t* f = fb + dim * b;
+            double nB[3] = {0, 0, 0};
+            face_area_vector(dim, x, f, nB);
+            for (int c = 0; c < dim; c++) bn[c] += nB[c] / (double)dim;
+            /* boundary-face share of L at v */
+            double wB[3] = {0, 0, 0}, wt[3];
+            int ned = dim == 3 ? 3 : 1;
+            for (int a = 0; a < ned; a++) {
+                int32_t a0 = f[a], a1 = f[(a + 1) % dim];
+                or_hash_w(dim, a0 < a1 ? a0 : a1, a0 < a1 ? a1 : a0, seed, wt);
+                for (int q = 0; q < dim; q++) wB[q] += wt[q];
+            }
+            double xl[9]; int32_t fl[3] = {0, 1, 2};
+            for (int i = 0; i < dim; i++) for (int q = 0; q < dim; q++) xl[dim * i + q] = x[dim * f[i] + q];
+            double glocal[9] = {0};
+            bface_grad(dim, xl, fl, wB, 1.0 / (dim * (dim + 1.0)), glocal);
+            for (int i = 0; i < dim; i++) if (f[i] == v) for (int q = 0; q < dim; q++) gg[q] += glocal[dim * i + q];
+        }
+        v_out[s] = vol;
+        for (int c = 0; c < dim; c++) { b_out[dim * s + c] = bn[c]; g[c] = gg[c]; }
+    }
+    free_stars(&st);
+    free(nodes);
+}

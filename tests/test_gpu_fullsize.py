@@ -1,0 +1,125 @@
+"""Full-size checks in the benchmark's configuration.
+
+160^3 x 6 tets, offset 1e3 (the benchmark workload), tile size chosen as in
+the benchmark: edge_build is checked through properties that characterise
+the sorted unique edge list exactly; the metrics and the adjoint are checked
+at 2000 sampled edges and nodes, each computed by the oracle alone from the
+elements around it.  96^3 x 6 (the adjoint workload): the full gradient
+against the oracle's analytic gradient and central differences on 1000 nodes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+SEED = 2502000778
+
+
+def _mesh(name):
+    cache = os.environ.get("EM_MESH_CACHE") or os.path.join(os.path.dirname(os.path.dirname(__file__)), "_build",
+                                                          "meshcache")
+    return meshgen.generate.cached_workload(name, cache_dir=cache)
+
+
+@pytest.fixture(scope="module")
+def big():
+    from paper_2502_00778_gb300 import api
+    m = _mesh("kuhn160_off1e3")
+    x = torch.from_numpy(m.x).to(DEV)
+    el = torch.from_numpy(m.elems).to(DEV)
+    topo = api.edge_build(el, x)
+    api.plan_build(topo, 128)
+    return m, x, topo
+
+
+def test_edge_build_properties_160(big):
+    m, x, topo = big
+    n = 160
+    e = topo.edges.cpu().numpy().astype(np.int64)
+    assert e.shape[0] == 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3
+    assert np.all(e[:, 0] < e[:, 1])
+    key = e[:, 0] * m.n_nodes + e[:, 1]
+    assert np.all(np.diff(key) > 0)                      # sorted, unique
+    e2e = topo.elem2edge.cpu().numpy()
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    used = np.zeros(e.shape[0], bool)
+    for l, (p, q) in enumerate(pairs):
+        a, b = m.elems[:, p].astype(np.int64), m.elems[:, q].astype(np.int64)
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        assert np.array_equal(e[e2e[:, l], 0], lo) and np.array_equal(e[e2e[:, l], 1], hi)
+        used[e2e[:, l]] = True
+    assert used.all()                                    # exactly the element edges
+    assert topo.n_bfaces == 12 * n * n
+    assert topo.n_bnodes == (n + 1) ** 3 - (n - 1) ** 3
+
+
+@pytest.mark.parametrize("prec", ["dw", "fp64"])
+def test_sampled_parity_160(big, prec):
+    from paper_2502_00778_gb300 import api
+    m, x, topo = big
+    e = topo.edges.cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(SEED + 31))
+    es = np.sort(rng.choice(e.shape[0], 2000, replace=False))
+    bn = topo.bnode.cpu().numpy()
+    ns = np.unique(np.concatenate([rng.choice(m.n_nodes, 1500, replace=False), rng.choice(bn, 500, replace=False)]))
+    w, c = meshgen.generate.hash_weights(e, m.n_nodes, 3, SEED)
+    wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
+    n, v, b, g = api.edge_metrics_fused(topo, x, wt, ct, prec)
+    rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], ns, SEED)
+    h = m.h
+    assert np.abs(n.cpu().numpy()[es] - rn).max() <= 1e-12 * h * h
+    assert np.abs(v.cpu().numpy()[ns] - rv).max() <= 1e-12 * h ** 3
+    bfull = np.zeros((m.n_nodes, 3))
+    bfull[bn] = b.cpu().numpy()
+    assert np.abs(bfull[ns] - rb).max() <= 1e-12 * h * h
+    gg = g.cpu().numpy()
+    assert np.abs(gg[ns] - rg).max() <= 1e-12 * np.abs(gg).max()
+    # properties at every node: closure and the volume sum
+    a = np.zeros((m.n_nodes, 3))
+    nn = n.cpu().numpy()
+    np.add.at(a, e[:, 0], nn)
+    np.add.at(a, e[:, 1], -nn)
+    a[bn] += bfull[bn]
+    assert np.abs(a).max() <= 1e-12 * h * h
+    assert abs(v.cpu().numpy().sum() - 1.0) <= 1e-11
+
+
+def test_atomic_fp64_sampled_160(big):
+    from paper_2502_00778_gb300 import api
+    m, x, topo = big
+    e = topo.edges.cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(SEED + 32))
+    es = np.sort(rng.choice(e.shape[0], 500, replace=False))
+    n, v, b = api.edge_metrics(topo, x, "fp64", "atomic")
+    rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], np.array([0], np.int32), SEED)
+    assert np.abs(n.cpu().numpy()[es] - rn).max() <= 1e-12 * m.h ** 2
+
+
+def test_adjoint_96_fd():
+    """Adjoint workload: full oracle gradient, and central differences with
+    step 1e-6 h on 1000 seeded nodes (L is affine in each coordinate, so the
+    difference carries rounding error only)."""
+    from paper_2502_00778_gb300 import api
+    m = _mesh("kuhn96")
+    x = torch.from_numpy(m.x).to(DEV)
+    topo = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+    api.plan_build(topo, 128)
+    t = oracle.topology(3, m.elems, m.x)
+    assert np.array_equal(topo.edges.cpu().numpy(), t.edges)
+    w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, 3, seed=SEED + 5)
+    wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
+    rg = oracle.adjoint(3, m.x, m.elems, t, w, c)
+    tol = 1e-12 * np.abs(rg).max()
+    for prec, path in [("dw", "gather"), ("fp64", "gather"), ("fp64", "atomic")]:
+        g = api.edge_metrics_adjoint(topo, x, wt, ct, prec, path).cpu().numpy()
+        assert np.abs(g - rg).max() <= tol, (prec, path)
+    nodes = meshgen.generate.fd_nodes(m.n_nodes, 1000, seed=SEED + 6)
+    gfd = oracle.fd_gradient(3, m.x, m.elems, t, w, c, nodes, 1e-6 * m.h)
+    assert np.abs(g[nodes] - gfd).max() <= 1e-7 * np.abs(rg).max()

@@ -53,8 +53,12 @@ def _or_too_big(fn):
 @pytest.mark.parametrize("tile", [32, 64, 128, 256, 512, 2048])
 @pytest.mark.parametrize("name", ["tri_odd", "kuhn7_off", "kuhn11_nomorton", "kuhn48"])
 def test_tile_sizes(name, tile):
-    from paper_2502_00778_gb300 import api
-    m, x, topo = _setup(name, tile)
+    from paper_2502_00778_gb300 import api, EMError
+    try:
+        m, x, topo = _setup(name, tile)
+    except EMError as ex:       # tiles beyond the 16-bit local index range are refused at plan build
+        assert "16-bit" in str(ex) and tile > 256, str(ex)
+        return
     rn, rv, rb = oracle_fwd(name)
     r = _or_too_big(lambda: api.edge_metrics(topo, x, "dw", "gather"))
     if r is not None:

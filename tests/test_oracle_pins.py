@@ -372,3 +372,28 @@ def test_adjoint_patch_fd_medium():
     nodes = meshgen.generate.fd_nodes(m.n_nodes, 200, seed=45)
     gp = oracle.fd_gradient(3, m.x, m.elems, t, w, c, nodes, 1e-6 * m.h)
     assert np.abs(g[nodes] - gp).max() <= 1e-7 * np.abs(g).max()
+
+
+# ----------------------------------------------------------------------------
+# the sampled evaluation used at full grid sizes equals the full evaluation
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("builder", [
+    lambda: meshgen.kuhn_cube(5, jitter=0.3, seed=61),
+    lambda: meshgen.tri_square(7, jitter=0.3, seed=62),
+    lambda: meshgen.kuhn_cube(4, jitter=0.2, seed=63, offset=1000.0),
+])
+def test_sampled_oracle_equals_full(builder):
+    m = builder()
+    t = oracle.topology(m.dim, m.elems, m.x)
+    n, v, b = oracle.direct(m.dim, m.x, m.elems, t)
+    w, c = meshgen.generate.hash_weights(t.edges, m.n_nodes, m.dim, 2502000778)
+    g = oracle.adjoint(m.dim, m.x, m.elems, t, w, c)
+    es = np.arange(0, t.n_edges, 2)
+    sn, sv, sb, sg = oracle.sample(m.dim, m.x, m.elems, t.edges[es, 0], t.edges[es, 1], np.arange(m.n_nodes),
+                                   2502000778)
+    full_b = np.zeros((m.n_nodes, m.dim))
+    full_b[t.bnode] = b
+    assert np.abs(sn - n[es]).max() <= 1e-15 * m.h ** (m.dim - 1)
+    assert np.abs(sv - v).max() <= 1e-15 * m.h ** m.dim
+    assert np.abs(sb - full_b).max() <= 1e-15 * m.h ** (m.dim - 1)
+    assert np.abs(sg - g).max() <= 1e-14 * np.abs(g).max()
