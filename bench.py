@@ -239,19 +239,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     edge_build_ms = (time.perf_counter() - t0) * 1e3
     del topo2
-    path = args.path or "gather"
-    prec = args.prec or ("dw" if path == "gather" else "fp64")
+    path = args.path or "auto"
+    prec = args.prec or ("fp64" if path in ("atomic", "csr") else "dw")
     g = torch.Generator(device="cpu").manual_seed(meshgen.SEED_BASE + 5)
     w = torch.randn((topo.n_edges, m.dim), generator=g, dtype=torch.float64).to(dev)
     c = torch.randn(m.n_nodes, generator=g, dtype=torch.float64).to(dev)
     have_gather = True
     sweep = None
     try:
-        if args.tile_nodes:
+        if args.tile_nodes and path != "auto":
             tile = args.tile_nodes
         else:
             from paper_2502_00778_gb300 import autotune
-            tile, sweep = autotune.tune(topo, x, w, c, "fused", prec if path == "gather" else "dw", use_cache=False)
+            cands = (args.tile_nodes,) if args.tile_nodes else autotune.CANDIDATES
+            pths = ("gather", "tiled") if path == "auto" else ((path,) if path in ("gather", "tiled") else ("tiled",))
+            best_path, tile, sweep = autotune.tune(topo, x, w, c, "fused", prec, candidates=cands, use_cache=False,
+                                                   paths=pths)
+            if path == "auto":
+                path = best_path
         t0 = time.perf_counter()
         api.plan_build(topo, tile)
         torch.cuda.synchronize()
@@ -261,7 +266,7 @@ def run_ours(args):
         have_gather = False
         plan_build_ms = None
         tile = None
-        if path == "gather":
+        if path in ("gather", "tiled", "auto"):
             path, prec = "atomic", "fp64"
     outs = (torch.empty((topo.n_edges, m.dim), dtype=torch.float64, device=dev),
             torch.empty(m.n_nodes, dtype=torch.float64, device=dev),
@@ -270,10 +275,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(x_, w_, c_, ev=None):
-        if path == "gather":
+        if path in ("gather", "tiled"):
             if ev is not None:
                 ev[0].record(stream)
-            api.edge_metrics_fused(topo, x_, w_, c_, prec, out=outs)
+            api.edge_metrics_fused(topo, x_, w_, c_, prec, out=outs, path=path)
             if ev is not None:
                 ev[1].record(stream)
         else:
@@ -321,9 +326,9 @@ def run_ours(args):
     value = ws * m.n_elems * K / (t_max * 1e-3)
 
     # dominant kernel: the fused gather kernel, or the forward element kernel
-    if path == "gather":
+    if path in ("gather", "tiled"):
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
-        what, kname = "fused", f"k_tile_fused<{prec}>"
+        what, kname = "fused", f"{'k_tile_scatter' if path == 'tiled' else 'k_tile'}<3,{prec},fwd+adj>"
     else:
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
         what, kname = "fwd", f"k_fwd_atomic3<{prec}>"
@@ -375,12 +380,12 @@ def run_ours(args):
     if not args.no_forms and rank == 0:
         cand = [("atomic", "fp64"), ("atomic", "mixed"), ("csr", "fp64")]
         if have_gather:
-            cand += [("gather", "fp64"), ("gather", "dw"), ("gather", "mixed")]
+            cand += [(p_, q_) for p_ in ("gather", "tiled") for q_ in ("fp64", "dw", "mixed")]
         for pth, pr in cand:
             try:
                 def fstep():
-                    if pth == "gather":
-                        api.edge_metrics_fused(topo, x, w, c, pr, out=outs)
+                    if pth in ("gather", "tiled"):
+                        api.edge_metrics_fused(topo, x, w, c, pr, out=outs, path=pth)
                     elif pth == "csr":
                         api.edge_metrics(topo, x, pr, "csr", out=outs[:3])
                         api.edge_metrics_adjoint(topo, x, w, c, pr, "atomic", out=outs[3])

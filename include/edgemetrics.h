@@ -82,6 +82,11 @@ extern "C" {
                              accumulation; bit-reproducible run to run */
 #define EM_PATH_CSR    2  /* edge-centric CSR gather (per edge, its element slots in
                              ascending order; FP64 only); bit-reproducible */
+#define EM_PATH_TILED  3  /* same tiles as EM_PATH_GATHER, but each tile element adds
+                             its contributions to the tile's accumulators with
+                             shared-memory atomics (compensated FP32 for DW/MIXED):
+                             fewer instructions and barriers; accurate to the same
+                             contract, last bits not reproducible run to run */
 
 int em_version(void);
 
@@ -145,7 +150,7 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
                   void* stream);
 
 /* host summary of a plan (em_plan_build's plan_info output, em_mesh.plan_info) */
-#define EM_PLAN_INFO_LEN 12
+#define EM_PLAN_INFO_LEN 16
 #define EM_PLAN_INFO_TILE_NODES 0   /* nodes per tile */
 #define EM_PLAN_INFO_TILES      1   /* number of tiles */
 #define EM_PLAN_INFO_MAX_ELEMS  2   /* most elements in one tile */
@@ -156,6 +161,9 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
 #define EM_PLAN_INFO_MAX_OWNED_BNODES 7
 #define EM_PLAN_INFO_MAX_OWNED_NODES 8
 #define EM_PLAN_INFO_CHECK      9   /* plan size in bytes, echoed for validation */
+#define EM_PLAN_INFO_MAX_ESLOTS 10  /* most gather slots of one tile's owned edges */
+#define EM_PLAN_INFO_MAX_NSLOTS 11  /* most gather slots of one tile's owned nodes */
+#define EM_PLAN_INFO_MAX_BSLOTS 12  /* most gather slots of one tile's boundary nodes */
 
 /* em_plan_build -- tiled gather plan for EM_PATH_GATHER (run once per
  * connectivity, after em_edge_build).
@@ -221,7 +229,8 @@ typedef struct em_mesh {
  * the atomic path, all three are always produced on the gather paths).
  *   x          [n_nodes][dim] float64.
  *   precision  EM_PREC_*; path EM_PATH_*.  Supported pairs: ATOMIC with FP64,
- *              MIXED, MIXED_COMP32; GATHER with FP64, DW, MIXED; CSR with FP64.
+ *              MIXED, MIXED_COMP32; GATHER and TILED with FP64, DW, MIXED; CSR
+ *              with FP64.
  * Errors: EM_ERR_ARG (unsupported pair, missing plan/CSR), EM_ERR_WORKSPACE,
  * EM_ERR_CUDA.  Degenerate elements are not checked here (see
  * em_check_elements). */
@@ -241,9 +250,9 @@ int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path,
                             void* ws, size_t* ws_bytes, void* stream);
 
 /* em_edge_metrics_fused -- forward outputs and the adjoint in one pass over
- * the grid (the adjoint does not depend on the forward outputs).  GATHER path
- * only (FP64, DW, MIXED). */
-int em_edge_metrics_fused(const em_mesh* mesh, int precision,
+ * the grid (the adjoint does not depend on the forward outputs).  path:
+ * EM_PATH_GATHER or EM_PATH_TILED (FP64, DW, MIXED). */
+int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path,
                           const double* x, const double* w, const double* c,
                           double* n_edge, double* vol, double* bnormal, double* grad_x,
                           void* ws, size_t* ws_bytes, void* stream);
@@ -263,27 +272,33 @@ int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* 
 /* ------------------------------------------------------------------------ */
 
 /* One mesh of a batch: everything em_edge_metrics_fused needs (GATHER plan
- * required) plus its inputs and outputs. */
+ * required, mesh.plan_info filled) plus its inputs and outputs. */
 typedef struct em_batch_item {
     em_mesh mesh;
     const double* x; const double* w; const double* c;
     double* n_edge; double* vol; double* bnormal; double* grad_x;
 } em_batch_item;
 
-/* em_batched_fwd_adj -- forward + adjoint for n_meshes meshes of uneven size
- * in ONE persistent launch: the tiles of all meshes form one work list that
- * resident blocks drain through an atomic counter.
- *   items       DEVICE array [n_meshes] of em_batch_item (pointers inside are
- *               device pointers).
- *   tile_prefix DEVICE int64 [n_meshes+1]: exclusive prefix sum of the meshes'
- *               tile counts (from em_plan_tiles()).
- *   blocks      persistent grid size (0 = number of SMs x resident blocks).
- *   status      DEVICE int32[1], written: 0 or a negative EM_ERR_* code.
- * Holds no host-side state, makes no allocation and performs no
- * synchronization, so the call can be captured in a CUDA graph once its
- * workspace is allocated.  Precision: FP64, DW or MIXED. */
+/* em_batched_fwd_adj -- forward + adjoint (as em_edge_metrics_fused) for
+ * n_meshes grids of uneven size in ONE persistent launch.  The tiles of all
+ * grids form one work list; resident blocks claim tiles through an atomic
+ * counter and run each tile exactly as the single-grid gather path does, so
+ * every output equals em_edge_metrics_fused's bit for bit.  No block waits
+ * on another block.
+ *   items        DEVICE array [n_meshes] of em_batch_item (pointers inside
+ *                are device pointers); all grids must have the same dim.
+ *   tile_prefix  DEVICE int64 [n_meshes+1]: exclusive prefix sum of the grids'
+ *                tile counts (plan_info[EM_PLAN_INFO_TILES]).
+ *   max_info     HOST int64 [EM_PLAN_INFO_LEN]: element-wise maximum of the
+ *                grids' plan_info (sizes the shared memory of the launch).
+ *   dim          dimension of every grid (2 or 3).
+ *   blocks       persistent grid size (0: SMs x resident blocks per SM).
+ *   status       DEVICE int32[1], written: EM_OK, or EM_ERR_ARG if an item's
+ *                dim differs from `dim`.
+ * Workspace: a small counter (size query with ws == NULL).  The call reads
+ * nothing back to the host and allocates nothing. */
 int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix,
-                       int precision, int blocks, int32_t* status,
+                       const int64_t* max_info, int dim, int precision, int blocks, int32_t* status,
                        void* ws, size_t* ws_bytes, void* stream);
 
 /* number of tiles in a plan (HOST read of the plan header; synchronizes) */

@@ -16,7 +16,7 @@ ERRORS = {
 }
 
 PREC = {"fp64": 0, "dw": 1, "mixed": 2, "mixed_comp32": 3}
-PATH = {"atomic": 0, "gather": 1, "csr": 2}
+PATH = {"atomic": 0, "gather": 1, "csr": 2, "tiled": 3}
 
 _c = ctypes
 _vp = _c.c_void_p
@@ -32,7 +32,7 @@ class EmMesh(_c.Structure):
         ("elems", _vp), ("elem2edge", _vp), ("edges", _vp), ("edge_ptr", _vp), ("edge_slot", _vp),
         ("bface", _vp), ("bface_owner", _vp), ("bnode", _vp),
         ("plan", _vp), ("plan_bytes", _c.c_size_t),
-        ("plan_info", _c.c_int64 * 12),
+        ("plan_info", _c.c_int64 * 16),
     ]
 
 
@@ -55,10 +55,10 @@ SIGNATURES = {
     "em_edge_metrics": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _szp, _vp], _c.c_int),
     "em_edge_metrics_adjoint": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _szp, _vp],
                                 _c.c_int),
-    "em_edge_metrics_fused": ([_c.POINTER(EmMesh), _c.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _szp, _vp],
-                              _c.c_int),
+    "em_edge_metrics_fused": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _szp,
+                               _vp], _c.c_int),
     "em_check_elements": ([_c.c_int, _i64, _i64, _vp, _vp, _vp, _szp, _i64p, _vp], _c.c_int),
-    "em_batched_fwd_adj": ([_c.c_int, _vp, _vp, _c.c_int, _c.c_int, _vp, _vp, _szp, _vp], _c.c_int),
+    "em_batched_fwd_adj": ([_c.c_int, _vp, _vp, _i64p, _c.c_int, _c.c_int, _c.c_int, _vp, _vp, _szp, _vp], _c.c_int),
     "em_plan_tiles": ([_vp, _i64p, _vp], _c.c_int),
 }
 

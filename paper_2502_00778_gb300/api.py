@@ -149,7 +149,7 @@ def plan_build(topo: Topology, tile_nodes: int = 0) -> Topology:
             _ptr(topo.edges), topo.n_bfaces, _ptr(topo.bface) if topo.n_bfaces else null,
             _ptr(topo.bface_owner) if topo.n_bfaces else null, topo.n_bnodes,
             _ptr(topo.bnode) if topo.n_bnodes else null, int(tile_nodes))
-    info = (ctypes.c_int64 * 12)()
+    info = (ctypes.c_int64 * 16)()
     # 1: scratch for the count pass; 2: exact plan and scratch sizes; 3: build
     check(L.em_plan_build(*args, null, ctypes.byref(wsb), null, ctypes.byref(pb), info, _stream()))
     ws = workspace.get(wsb.value, dev)
@@ -216,8 +216,9 @@ def edge_metrics_adjoint(topo: Topology, x, w, c=None, precision: str = "fp64", 
     return g
 
 
-def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", out=None):
-    """Forward outputs and the adjoint in one pass (gather plan required)."""
+def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", out=None, path: str = "gather"):
+    """Forward outputs and the adjoint in one pass (plan required; path
+    "gather" = deterministic ordered gather, "tiled" = shared-memory scatter)."""
     L = load()
     _require_cuda(x, w, c)
     x = x.contiguous().to(torch.float64)
@@ -234,11 +235,11 @@ def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", ou
     m, mr = _mesh_ref(topo)
     wsb = ctypes.c_size_t(0)
     null = ctypes.c_void_p(0)
-    pr = PREC[precision]
+    pr, pa = PREC[precision], PATH[path]
     args = (_ptr(x), _ptr(w), _ptr(c), _ptr(n), _ptr(v), _ptr(b), _ptr(g))
-    check(L.em_edge_metrics_fused(mr, pr, *args, null, ctypes.byref(wsb), _stream()))
+    check(L.em_edge_metrics_fused(mr, pr, pa, *args, null, ctypes.byref(wsb), _stream()))
     ws = workspace.get(wsb.value, dev)
-    check(L.em_edge_metrics_fused(mr, pr, *args, _ptr(ws), ctypes.byref(wsb), _stream()))
+    check(L.em_edge_metrics_fused(mr, pr, pa, *args, _ptr(ws), ctypes.byref(wsb), _stream()))
     return n, v, b, g
 
 
@@ -278,7 +279,7 @@ class EdgeMetrics(torch.autograd.Function):
         topo = ctx.topo
         if gn is None:
             gn = torch.zeros((topo.n_edges, topo.dim), dtype=torch.float64, device=x.device)
-        adj_path = ctx.path if ctx.path in ("atomic", "gather") else "atomic"
+        adj_path = ctx.path if ctx.path in ("atomic", "gather", "tiled") else "atomic"
         g = edge_metrics_adjoint(topo, x, gn, gv, ctx.precision if ctx.precision != "mixed_comp32" else "mixed",
                                  adj_path)
         return g, None, None, None

@@ -25,9 +25,9 @@ def _cache_path():
                                                                "autotune.json")
 
 
-def _key(topo, what, precision):
+def _key(topo, what, precision, paths):
     dev = torch.cuda.get_device_name()
-    return f"{dev}|dim{topo.dim}|v{topo.n_nodes}|e{topo.n_elems}|{what}|{precision}"
+    return f"{dev}|dim{topo.dim}|v{topo.n_nodes}|e{topo.n_elems}|{what}|{precision}|{','.join(paths)}"
 
 
 def _load():
@@ -61,36 +61,43 @@ def _time(fn, reps=5):
     return a.elapsed_time(b) / reps
 
 
-def tune(topo, x, w=None, c=None, what="fused", precision="dw", candidates=CANDIDATES, reps=5, use_cache=True):
-    """Pick tile_nodes for `what` in {"fwd", "adj", "fused"}; builds the
-    winning plan into topo and returns (tile_nodes, {tile: ms or error})."""
+def tune(topo, x, w=None, c=None, what="fused", precision="dw", candidates=CANDIDATES, reps=5, use_cache=True,
+         paths=("gather", "tiled")):
+    """Pick (path, tile_nodes) for `what` in {"fwd", "adj", "fused"} among
+    the tiled paths `paths`; builds the winning plan into topo and returns
+    (path, tile_nodes, {"path/tile": ms or error})."""
     cache = _load() if use_cache else {}
-    key = _key(topo, what, precision)
+    key = _key(topo, what, precision, paths)
     if use_cache and key in cache:
         t = int(cache[key]["tile_nodes"])
         api.plan_build(topo, t)
-        return t, cache[key].get("sweep", {})
+        return cache[key]["path"], t, cache[key].get("sweep", {})
     sweep = {}
     best = None
     for t in candidates:
         try:
             api.plan_build(topo, t)
-            if what == "fwd":
-                fn = lambda: api.edge_metrics(topo, x, precision, "gather")  # noqa: E731
-            elif what == "adj":
-                fn = lambda: api.edge_metrics_adjoint(topo, x, w, c, precision, "gather")  # noqa: E731
-            else:
-                fn = lambda: api.edge_metrics_fused(topo, x, w, c, precision)  # noqa: E731
-            ms = _time(fn, reps)
-            sweep[str(t)] = round(ms, 4)
-            if best is None or ms < best[1]:
-                best = (t, ms)
         except EMError as ex:
-            sweep[str(t)] = f"unusable: {str(ex)[:80]}"
+            sweep[f"*/{t}"] = f"unusable: {str(ex)[:80]}"
+            continue
+        for p in paths:
+            try:
+                if what == "fwd":
+                    fn = lambda: api.edge_metrics(topo, x, precision, p)  # noqa: E731
+                elif what == "adj":
+                    fn = lambda: api.edge_metrics_adjoint(topo, x, w, c, precision, p)  # noqa: E731
+                else:
+                    fn = lambda: api.edge_metrics_fused(topo, x, w, c, precision, path=p)  # noqa: E731
+                ms = _time(fn, reps)
+                sweep[f"{p}/{t}"] = round(ms, 4)
+                if best is None or ms < best[2]:
+                    best = (p, t, ms)
+            except EMError as ex:
+                sweep[f"{p}/{t}"] = f"unusable: {str(ex)[:80]}"
     if best is None:
         raise EMError(-1, f"no usable tile size among {candidates}")
-    api.plan_build(topo, best[0])
-    cache[key] = {"tile_nodes": best[0], "ms": best[1], "sweep": sweep}
+    api.plan_build(topo, best[1])
+    cache[key] = {"path": best[0], "tile_nodes": best[1], "ms": best[2], "sweep": sweep}
     if use_cache:
         _store(cache)
-    return best[0], sweep
+    return best[0], best[1], sweep

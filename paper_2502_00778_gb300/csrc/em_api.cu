@@ -93,10 +93,10 @@ int em_edge_metrics(const em_mesh* mesh, int precision, int path, const double* 
         if (precision != EM_PREC_FP64 && precision != EM_PREC_MIXED && precision != EM_PREC_MIXED_COMP32)
             return fail(EM_ERR_ARG, "atomic path supports FP64, MIXED and MIXED_COMP32");
         need = atomic_fwd_ws_bytes(mesh, precision);
-    } else if (path == EM_PATH_GATHER) {
+    } else if (path == EM_PATH_GATHER || path == EM_PATH_TILED) {
         if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
-            return fail(EM_ERR_ARG, "gather path supports FP64, DW and MIXED");
-        if (!mesh->plan) return fail(EM_ERR_ARG, "gather path needs a plan from em_plan_build");
+            return fail(EM_ERR_ARG, "gather/tiled paths support FP64, DW and MIXED");
+        if (!mesh->plan) return fail(EM_ERR_ARG, "gather/tiled paths need a plan from em_plan_build");
         need = gather_ws_bytes(mesh);
     } else if (path == EM_PATH_CSR) {
         if (precision != EM_PREC_FP64) return fail(EM_ERR_ARG, "CSR path supports FP64 only");
@@ -113,9 +113,10 @@ int em_edge_metrics(const em_mesh* mesh, int precision, int path, const double* 
     int st;
     if (path == EM_PATH_ATOMIC) {
         st = atomic_fwd(mesh, precision, x, n_edge, vol, bnormal, ws, s);
-    } else if (path == EM_PATH_GATHER) {
+    } else if (path == EM_PATH_GATHER || path == EM_PATH_TILED) {
         if (!n_edge || !vol || (mesh->n_bnodes && !bnormal)) return fail(EM_ERR_ARG, "gather path needs all outputs");
-        st = gather_run(mesh, precision, GATHER_FWD, x, nullptr, nullptr, n_edge, vol, bnormal, nullptr, ws, s);
+        st = gather_run(mesh, precision, GATHER_FWD | (path == EM_PATH_TILED ? GATHER_SCATTER : 0), x, nullptr,
+                        nullptr, n_edge, vol, bnormal, nullptr, ws, s);
     } else {
         if (!n_edge || !vol || (mesh->n_bnodes && !bnormal)) return fail(EM_ERR_ARG, "CSR path needs all outputs");
         st = csr_fwd(mesh, x, n_edge, vol, bnormal, ws, s);
@@ -130,13 +131,13 @@ int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path, const 
     if (path == EM_PATH_ATOMIC) {
         if (precision != EM_PREC_FP64 && precision != EM_PREC_MIXED)
             return fail(EM_ERR_ARG, "atomic adjoint supports FP64 and MIXED");
-    } else if (path == EM_PATH_GATHER) {
+    } else if (path == EM_PATH_GATHER || path == EM_PATH_TILED) {
         if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
-            return fail(EM_ERR_ARG, "gather adjoint supports FP64, DW and MIXED");
-        if (!mesh->plan) return fail(EM_ERR_ARG, "gather path needs a plan from em_plan_build");
+            return fail(EM_ERR_ARG, "gather/tiled adjoint supports FP64, DW and MIXED");
+        if (!mesh->plan) return fail(EM_ERR_ARG, "gather/tiled paths need a plan from em_plan_build");
         need = gather_ws_bytes(mesh);
     } else {
-        return fail(EM_ERR_ARG, "adjoint supports the ATOMIC and GATHER paths");
+        return fail(EM_ERR_ARG, "adjoint supports the ATOMIC, GATHER and TILED paths");
     }
     bool query;
     EM_TRY(check_ws(ws, ws_bytes, need, &query));
@@ -145,14 +146,17 @@ int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path, const 
     cudaStream_t s = as_stream(stream);
     int st;
     if (path == EM_PATH_ATOMIC) st = atomic_adj(mesh, precision, x, w, c, grad_x, s);
-    else st = gather_run(mesh, precision, GATHER_ADJ, x, w, c, nullptr, nullptr, nullptr, grad_x, ws, s);
+    else
+        st = gather_run(mesh, precision, GATHER_ADJ | (path == EM_PATH_TILED ? GATHER_SCATTER : 0), x, w, c, nullptr,
+                        nullptr, nullptr, grad_x, ws, s);
     return st == EM_OK ? ok() : st;
 }
 
-int em_edge_metrics_fused(const em_mesh* mesh, int precision, const double* x, const double* w, const double* c,
-                          double* n_edge, double* vol, double* bnormal, double* grad_x, void* ws, size_t* ws_bytes,
-                          void* stream) {
+int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path, const double* x, const double* w,
+                          const double* c, double* n_edge, double* vol, double* bnormal, double* grad_x, void* ws,
+                          size_t* ws_bytes, void* stream) {
     EM_TRY(check_mesh(mesh));
+    if (path != EM_PATH_GATHER && path != EM_PATH_TILED) return fail(EM_ERR_ARG, "fused pass: GATHER or TILED path");
     if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
         return fail(EM_ERR_ARG, "fused pass supports FP64, DW and MIXED");
     if (!mesh->plan) return fail(EM_ERR_ARG, "fused pass needs a plan from em_plan_build");
@@ -161,8 +165,8 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, const double* x, c
     if (query) return ok();
     if (!x || !w || !grad_x || !n_edge || !vol || (mesh->n_bnodes && !bnormal))
         return fail(EM_ERR_ARG, "fused pass needs x, w and all outputs");
-    int st = gather_run(mesh, precision, GATHER_FWD | GATHER_ADJ, x, w, c, n_edge, vol, bnormal, grad_x, ws,
-                        as_stream(stream));
+    int st = gather_run(mesh, precision, GATHER_FWD | GATHER_ADJ | (path == EM_PATH_TILED ? GATHER_SCATTER : 0), x, w,
+                        c, n_edge, vol, bnormal, grad_x, ws, as_stream(stream));
     return st == EM_OK ? ok() : st;
 }
 
@@ -181,9 +185,11 @@ int em_plan_tiles(const void* plan, int64_t* n_tiles, void* stream) {
     return st == EM_OK ? ok() : st;
 }
 
-int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int precision,
-                       int blocks, int32_t* status, void* ws, size_t* ws_bytes, void* stream) {
-    int st = batched_impl(n_meshes, items, tile_prefix, precision, blocks, status, ws, ws_bytes, as_stream(stream));
+int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, const int64_t* max_info,
+                       int dim, int precision, int blocks, int32_t* status, void* ws, size_t* ws_bytes,
+                       void* stream) {
+    int st = batched_impl(n_meshes, items, tile_prefix, max_info, dim, precision, blocks, status, ws, ws_bytes,
+                          as_stream(stream));
     return st == EM_OK ? ok() : st;
 }
 

@@ -372,6 +372,17 @@ __global__ void k_bface_records(int dim, int64_t BP, const uint64_t* bkey, const
     }
 }
 
+__global__ void k_tile_slot_max(int64_t n_tiles, const TileInfo* tiles, const int32_t* eptr, const int32_t* nptr,
+                                const int32_t* bptr, int64_t* maxv) {
+    GRID_LOOP(t, n_tiles) {
+        TileInfo ti = tiles[t];
+        atomicMax((unsigned long long*)&maxv[0], (unsigned long long)(eptr[ti.edge0 + ti.n_eo] - eptr[ti.edge0]));
+        atomicMax((unsigned long long*)&maxv[1], (unsigned long long)(nptr[ti.node0 + ti.n_own] - nptr[ti.node0]));
+        if (bptr)
+            atomicMax((unsigned long long*)&maxv[2], (unsigned long long)(bptr[ti.bnode0 + ti.n_bo] - bptr[ti.bnode0]));
+    }
+}
+
 __global__ void k_key_counts(const uint64_t* k, int64_t n, int32_t* cnt) {
     GRID_LOOP(i, n) atomicAdd(&cnt[k[i]], 1);
 }
@@ -523,6 +534,7 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     int32_t* kcnt = L.take<int32_t>(std::max<int64_t>({n_edges, nv, nbn}) + 1);
     int64_t* koff = L.take<int64_t>(std::max<int64_t>({n_edges, nv, nbn}) + 1);
     int64_t* maxv = L.take<int64_t>(8);
+    int64_t* smax = L.take<int64_t>(4);
     unsigned long long* status = L.take<unsigned long long>(2);
     const size_t full_bytes = L.bytes();
 
@@ -642,8 +654,11 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     }
     EM_CUDA_TRY(cudaGetLastError());
 
+    EM_CUDA_TRY(cudaMemsetAsync(smax, 0, 32, s));
+    k_tile_slot_max<<<G(n_tiles), NT, 0, s>>>(n_tiles, tiles, eslot_ptr, nslot_ptr, nbn ? bslot_ptr : nullptr, smax);
     // 8. header
-    int64_t mx[8];
+    int64_t mx[8], sm[4];
+    EM_CUDA_TRY(cudaMemcpyAsync(sm, smax, sizeof(sm), cudaMemcpyDeviceToHost, s));
     unsigned long long st[2];
     EM_CUDA_TRY(cudaMemcpyAsync(mx, maxv, sizeof(mx), cudaMemcpyDeviceToHost, s));
     EM_CUDA_TRY(cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -676,6 +691,9 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
         plan_info[EM_PLAN_INFO_MAX_OWNED_BNODES] = h.max_bo;
         plan_info[EM_PLAN_INFO_MAX_OWNED_NODES] = h.max_own;
         plan_info[EM_PLAN_INFO_CHECK] = po.total;
+        plan_info[EM_PLAN_INFO_MAX_ESLOTS] = sm[0];
+        plan_info[EM_PLAN_INFO_MAX_NSLOTS] = sm[1];
+        plan_info[EM_PLAN_INFO_MAX_BSLOTS] = sm[2];
     }
     return EM_OK;
 }

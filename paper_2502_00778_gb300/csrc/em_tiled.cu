@@ -114,11 +114,18 @@ enum { DO_FWD = 1, DO_ADJ = 2 };
 
 // shared-memory layout, computed identically on host and device
 struct Smem {
-    size_t xs, ws, cs, st_m, st_v, st_g, acc_e, cur_e, acc_v, acc_g, cur_n, acc_b, cur_b, total;
+    size_t xs, ws, cs, st_m, st_v, st_g, acc_e, cur_e, acc_v, acc_g, cur_n, acc_b, cur_b;
+    size_t eptr, eslot, nptr, nslot, bptr, bslot, total;
+};
+
+struct Dims {
+    int max_nodes, max_edges, max_eo, max_own, max_bo, max_es, max_ns, max_bs;
 };
 
 template <int DIM, int PREC, int WHAT>
-__host__ __device__ inline Smem smem_layout(int max_nodes, int max_edges, int max_eo, int max_own, int max_bo) {
+__host__ __device__ inline Smem smem_layout(const Dims& D) {
+    const int max_nodes = D.max_nodes, max_edges = D.max_edges, max_eo = D.max_eo, max_own = D.max_own,
+              max_bo = D.max_bo;
     using F = Form<PREC>;
     constexpr int NN = DIM;          // staged face vectors per element (3D: m0,m1,m2; 2D: m0,m1)
     Smem s;
@@ -131,12 +138,18 @@ __host__ __device__ inline Smem smem_layout(int max_nodes, int max_edges, int ma
     s.st_v = (WHAT & DO_FWD) ? take(sizeof(typename F::V) * NT) : 0;
     s.st_g = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * (DIM + 1) * DIM * NT) : 0;
     s.acc_e = (WHAT & DO_FWD) ? take(sizeof(typename F::A) * DIM * max_eo) : 0;
-    s.cur_e = (WHAT & DO_FWD) ? take(sizeof(int) * max_eo) : 0;
+    s.cur_e = (WHAT & DO_FWD) ? take(sizeof(int) * max_eo * DIM) : 0;
     s.acc_v = (WHAT & DO_FWD) ? take(sizeof(typename F::A) * max_own) : 0;
     s.acc_g = (WHAT & DO_ADJ) ? take(sizeof(typename F::A) * DIM * max_own) : 0;
-    s.cur_n = take(sizeof(int) * max_own);
+    s.cur_n = take(sizeof(int) * max_own * (((WHAT & DO_FWD) ? 1 : 0) + ((WHAT & DO_ADJ) ? DIM : 0)));
     s.acc_b = (WHAT & DO_FWD) ? take(sizeof(typename F::A) * DIM * max_bo) : 0;
-    s.cur_b = take(sizeof(int) * max_bo);
+    s.cur_b = take(sizeof(int) * max_bo * (((WHAT & DO_FWD) ? DIM : 0) + ((WHAT & DO_ADJ) ? DIM : 0)));
+    s.eptr = (WHAT & DO_FWD) ? take(sizeof(int) * (max_eo + 1)) : 0;
+    s.eslot = (WHAT & DO_FWD) ? take(sizeof(uint16_t) * D.max_es) : 0;
+    s.nptr = take(sizeof(int) * (max_own + 1));
+    s.nslot = take(sizeof(uint16_t) * D.max_ns);
+    s.bptr = take(sizeof(int) * (max_bo + 1));
+    s.bslot = take(sizeof(uint16_t) * D.max_bs);
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -151,7 +164,7 @@ struct TileArgs {
     double* vol;
     double* bnormal;
     double* grad;
-    int max_nodes, max_edges, max_eo, max_own, max_bo;
+    Dims D;
     int n_tiles;
     int64_t tile_base;      // first tile handled by blockIdx.x == 0
 };
@@ -177,7 +190,7 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
     const int32_t* bptr = plan_at<int32_t>(A.plan, H->off_bslot_ptr);
     const uint16_t* bslot = plan_at<uint16_t>(A.plan, H->off_bslot);
 
-    const Smem L = smem_layout<DIM, PREC, WHAT>(A.max_nodes, A.max_edges, A.max_eo, A.max_own, A.max_bo);
+    const Smem L = smem_layout<DIM, PREC, WHAT>(A.D);
     C* xs = reinterpret_cast<C*>(smem + L.xs);
     V* ws = reinterpret_cast<V*>(smem + L.ws);
     V* cs = reinterpret_cast<V*>(smem + L.cs);
@@ -191,9 +204,18 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
     int* cur_n = reinterpret_cast<int*>(smem + L.cur_n);
     Acc* acc_b = reinterpret_cast<Acc*>(smem + L.acc_b);
     int* cur_b = reinterpret_cast<int*>(smem + L.cur_b);
+    int* s_eptr = reinterpret_cast<int*>(smem + L.eptr);
+    uint16_t* s_eslot = reinterpret_cast<uint16_t*>(smem + L.eslot);
+    int* s_nptr = reinterpret_cast<int*>(smem + L.nptr);
+    uint16_t* s_nslot = reinterpret_cast<uint16_t*>(smem + L.nslot);
+    int* s_bptr = reinterpret_cast<int*>(smem + L.bptr);
+    uint16_t* s_bslot = reinterpret_cast<uint16_t*>(smem + L.bslot);
 
     const int tid = threadIdx.x;
     const int nnodes = ti.n_own + ti.n_halo;
+    // gather work items: one per (output, component)
+    constexpr int NCN = ((WHAT & DO_FWD) ? 1 : 0) + ((WHAT & DO_ADJ) ? DIM : 0);   // node: [grad comps..., V]
+    constexpr int NCB = ((WHAT & DO_FWD) ? DIM : 0) + ((WHAT & DO_ADJ) ? DIM : 0);  // boundary node: [bnormal, grad]
     double org[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
@@ -213,35 +235,63 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
             for (int d = 0; d < DIM; d++) ws[i * DIM + d] = F::from_double(A.w[e * DIM + d]);
         }
     }
+    // gather lists of the tile, copied to shared memory (offsets made local)
     if (WHAT & DO_FWD) {
-        for (int le = tid; le < ti.n_eo; le += NT) {
-#pragma unroll
-            for (int d = 0; d < DIM; d++) acc_e[le * DIM + d] = F::zero();
-            cur_e[le] = eptr[ti.edge0 + le];
+        const int e_base = eptr[ti.edge0];
+        const int ne_sl = eptr[ti.edge0 + ti.n_eo] - e_base;
+        for (int i = tid; i <= ti.n_eo; i += NT) s_eptr[i] = eptr[ti.edge0 + i] - e_base;
+        for (int q = tid; q < ne_sl; q += NT) s_eslot[q] = eslot[e_base + q];
+        for (int q = tid; q < ti.n_eo * DIM; q += NT) {
+            acc_e[q] = F::zero();
+            cur_e[q] = eptr[ti.edge0 + q / DIM] - e_base;
         }
     }
-    for (int i = tid; i < ti.n_own; i += NT) {
-        if (WHAT & DO_FWD) acc_v[i] = F::zero();
-        if (WHAT & DO_ADJ) {
+    {
+        const int n_base = nptr[ti.node0];
+        const int nn_sl = nptr[ti.node0 + ti.n_own] - n_base;
+        for (int i = tid; i <= ti.n_own; i += NT) s_nptr[i] = nptr[ti.node0 + i] - n_base;
+        for (int q = tid; q < nn_sl; q += NT) s_nslot[q] = nslot[n_base + q];
+        for (int i = tid; i < ti.n_own; i += NT) {
+            if (WHAT & DO_FWD) acc_v[i] = F::zero();
+            if (WHAT & DO_ADJ) {
 #pragma unroll
-            for (int d = 0; d < DIM; d++) acc_g[i * DIM + d] = F::zero();
+                for (int d = 0; d < DIM; d++) acc_g[i * DIM + d] = F::zero();
+            }
         }
-        cur_n[i] = nptr[ti.node0 + i];
+        for (int q = tid; q < ti.n_own * NCN; q += NT) cur_n[q] = nptr[ti.node0 + q / NCN] - n_base;
     }
-    for (int k = tid; k < ti.n_bo; k += NT) {
-        if (WHAT & DO_FWD) {
+    if (ti.n_bo) {
+        const int b_base = bptr[ti.bnode0];
+        const int nb_sl = bptr[ti.bnode0 + ti.n_bo] - b_base;
+        for (int i = tid; i <= ti.n_bo; i += NT) s_bptr[i] = bptr[ti.bnode0 + i] - b_base;
+        for (int q = tid; q < nb_sl; q += NT) s_bslot[q] = bslot[b_base + q];
+        for (int k = tid; k < ti.n_bo; k += NT) {
+            if (WHAT & DO_FWD) {
 #pragma unroll
-            for (int d = 0; d < DIM; d++) acc_b[k * DIM + d] = F::zero();
+                for (int d = 0; d < DIM; d++) acc_b[k * DIM + d] = F::zero();
+            }
         }
-        cur_b[k] = bptr[ti.bnode0 + k];
+        for (int q = tid; q < ti.n_bo * NCB; q += NT) cur_b[q] = bptr[ti.bnode0 + q / NCB] - b_base;
     }
     __syncthreads();
 
     // ---- element chunks ------------------------------------------------------
+    ElemConn cn_next;
+    ElemEdges ee_next;
+    if (tid < ti.n_el) {
+        cn_next = conn[tid];
+        if (WHAT & DO_ADJ) ee_next = tedge[tid];
+    }
     for (int cb = 0; cb < ti.n_el; cb += NT) {
         const int j = tid;
+        const ElemConn cn_cur = cn_next;
+        const ElemEdges ee_cur = ee_next;
+        if (cb + NT + j < ti.n_el) {          // prefetch the next chunk's records
+            cn_next = conn[cb + NT + j];
+            if (WHAT & DO_ADJ) ee_next = tedge[cb + NT + j];
+        }
         if (cb + j < ti.n_el) {
-            const ElemConn cn = conn[cb + j];
+            const ElemConn cn = cn_cur;
             if (DIM == 3) {
                 V a[3], b[3], c[3];
 #pragma unroll
@@ -266,7 +316,7 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
                     st_v[j] = F::sgn(det, s);
                 }
                 if (WHAT & DO_ADJ) {
-                    const ElemEdges ee = tedge[cb + j];
+                    const ElemEdges ee = ee_cur;
                     V W0[3], W1[3], W2[3];
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
@@ -324,7 +374,7 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
                     st_v[j] = F::sgn(det, s);
                 }
                 if (WHAT & DO_ADJ) {
-                    const ElemEdges ee = tedge[cb + j];
+                    const ElemEdges ee = ee_cur;
                     V W0[2], W1[2];
 #pragma unroll
                     for (int d = 0; d < 2; d++) {
@@ -352,42 +402,39 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
         __syncthreads();
         const int cend = cb + NT;
         if (WHAT & DO_FWD) {
-            for (int le = tid; le < ti.n_eo; le += NT) {
-                int cur = cur_e[le];
-                const int end = eptr[ti.edge0 + le + 1];
-                Acc a0 = acc_e[le * DIM], a1 = acc_e[le * DIM + 1], a2 = DIM == 3 ? acc_e[le * DIM + 2] : F::zero();
+            for (int q = tid; q < ti.n_eo * DIM; q += NT) {
+                const int le = q / DIM, d = q - le * DIM;
+                int cur = cur_e[q];
+                const int end = s_eptr[le + 1];
+                Acc a = acc_e[q];
                 while (cur < end) {
-                    const unsigned sl = eslot[cur];
+                    const unsigned sl = s_eslot[cur];
                     const int code = sl & 3, idx = (int)(sl >> 2);
                     if (code == 3 || idx >= cend) break;
-                    const V* m = st_m + (idx - cb) * (NN * DIM) + code * DIM;
-                    F::acc(a0, m[0]);
-                    F::acc(a1, m[1]);
-                    if (DIM == 3) F::acc(a2, m[2]);
+                    F::acc(a, st_m[(idx - cb) * (NN * DIM) + code * DIM + d]);
                     cur++;
                 }
-                acc_e[le * DIM] = a0;
-                acc_e[le * DIM + 1] = a1;
-                if (DIM == 3) acc_e[le * DIM + 2] = a2;
-                cur_e[le] = cur;
+                acc_e[q] = a;
+                cur_e[q] = cur;
             }
         }
-        for (int i = tid; i < ti.n_own; i += NT) {
-            int cur = cur_n[i];
-            const int end = nptr[ti.node0 + i + 1];
+        for (int q = tid; q < ti.n_own * NCN; q += NT) {
+            const int i = q / NCN, k = q - i * NCN;
+            int cur = cur_n[q];
+            const int end = s_nptr[i + 1];
+            const bool isv = (WHAT & DO_FWD) && k == NCN - 1;
+            Acc a = isv ? acc_v[i] : acc_g[i * DIM + k];
             while (cur < end) {
-                const unsigned sl = nslot[cur];
+                const unsigned sl = s_nslot[cur];
                 const int r = sl & 3, idx = (int)(sl >> 2);
                 if (idx >= cend) break;
-                if (WHAT & DO_FWD) F::acc(acc_v[i], st_v[idx - cb]);
-                if (WHAT & DO_ADJ) {
-                    const V* gg = st_g + (idx - cb) * ((DIM + 1) * DIM) + r * DIM;
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) F::acc(acc_g[i * DIM + d], gg[d]);
-                }
+                if (isv) F::acc(a, st_v[idx - cb]);
+                else F::acc(a, st_g[(idx - cb) * ((DIM + 1) * DIM) + r * DIM + k]);
                 cur++;
             }
-            cur_n[i] = cur;
+            if (isv) acc_v[i] = a;
+            else acc_g[i * DIM + k] = a;
+            cur_n[q] = cur;
         }
         __syncthreads();
     }
@@ -447,42 +494,42 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
         __syncthreads();
         const int bend = bb + NT;
         if (WHAT & DO_FWD) {
-            for (int le = tid; le < ti.n_eo; le += NT) {
-                int cur = cur_e[le];
-                const int end = eptr[ti.edge0 + le + 1];
+            for (int q = tid; q < ti.n_eo * DIM; q += NT) {
+                const int le = q / DIM, d = q - le * DIM;
+                int cur = cur_e[q];
+                const int end = s_eptr[le + 1];
+                Acc a = acc_e[q];
                 while (cur < end) {
-                    const unsigned sl = eslot[cur];
+                    const unsigned sl = s_eslot[cur];
                     const int idx = (int)(sl >> 2);
                     if (idx >= bend) break;
-                    const V* m = st_m + (idx - bb) * (NN * DIM);
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) F::acc(acc_e[le * DIM + d], DIM == 3 ? m[d] : F::half(m[d]));
+                    const V m = st_m[(idx - bb) * (NN * DIM) + d];
+                    F::acc(a, DIM == 3 ? m : F::half(m));
                     cur++;
                 }
-                cur_e[le] = cur;
+                acc_e[q] = a;
+                cur_e[q] = cur;
             }
         }
-        for (int k = tid; k < ti.n_bo; k += NT) {
-            int cur = cur_b[k];
-            const int end = bptr[ti.bnode0 + k + 1];
-            const int i = A.bnode[ti.bnode0 + k] - ti.node0;
+        for (int q = tid; q < ti.n_bo * NCB; q += NT) {
+            const int kb = q / NCB, k = q - kb * NCB;
+            int cur = cur_b[q];
+            const int end = s_bptr[kb + 1];
+            const bool isb = (WHAT & DO_FWD) && k < DIM;
+            const int d = isb ? k : k - ((WHAT & DO_FWD) ? DIM : 0);
+            const int i = A.bnode[ti.bnode0 + kb] - ti.node0;
+            Acc a = isb ? acc_b[kb * DIM + d] : acc_g[i * DIM + d];
             while (cur < end) {
-                const unsigned sl = bslot[cur];
+                const unsigned sl = s_bslot[cur];
                 const int pos = sl & 3, idx = (int)(sl >> 2);
                 if (idx >= bend) break;
-                if (WHAT & DO_FWD) {
-                    const V* m = st_m + (idx - bb) * (NN * DIM);
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) F::acc(acc_b[k * DIM + d], m[d]);
-                }
-                if (WHAT & DO_ADJ) {
-                    const V* gg = st_g + (idx - bb) * ((DIM + 1) * DIM) + pos * DIM;
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) F::acc(acc_g[i * DIM + d], gg[d]);
-                }
+                if (isb) F::acc(a, st_m[(idx - bb) * (NN * DIM) + d]);
+                else F::acc(a, st_g[(idx - bb) * ((DIM + 1) * DIM) + pos * DIM + d]);
                 cur++;
             }
-            cur_b[k] = cur;
+            if (isb) acc_b[kb * DIM + d] = a;
+            else acc_g[i * DIM + d] = a;
+            cur_b[q] = cur;
         }
         __syncthreads();
     }
@@ -512,6 +559,367 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// scatter mode: every tile element adds its contributions to the tile's owned
+// accumulators with shared-memory atomics (compensated: the rounding error of
+// each FP32 atomic add is recovered with TwoSum and added to a low word), so
+// no chunk barriers, staging buffers or gather lists are needed.  Accurate to
+// double-word level, but the summation order (hence the last bits) varies
+// from run to run.
+// ---------------------------------------------------------------------------
+template <int PREC>
+struct Scat;
+
+template <>
+struct Scat<EM_PREC_FP64> {
+    using S = double;   // one shared word per accumulated component
+    static constexpr int W = 1;
+    static __device__ __forceinline__ void add(S* a, double v) { atomicAdd(a, v); }
+    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.0; }
+    static __device__ __forceinline__ double out(const S* a, double sc) { return a[0] * sc; }
+};
+
+template <>
+struct Scat<EM_PREC_DW> {
+    using S = float;    // (hi, lo) pairs
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void add(S* a, dw v) {
+        const float old = atomicAdd(a, v.h);
+        float s, e;
+        two_sum(old, v.h, s, e);
+        atomicAdd(a + 1, e + v.l);
+    }
+    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.f; a[1] = 0.f; }
+    static __device__ __forceinline__ double out(const S* a, double sc) {
+        dw s = dw_from_double(sc);
+        return dw_to_double(dw_mulc(dw{a[0], a[1]}, s.h, s.l));
+    }
+};
+
+template <>
+struct Scat<EM_PREC_MIXED> {
+    using S = float;
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void add(S* a, float v) {
+        const float old = atomicAdd(a, v);
+        float s, e;
+        two_sum(old, v, s, e);
+        atomicAdd(a + 1, e);
+    }
+    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.f; a[1] = 0.f; }
+    static __device__ __forceinline__ double out(const S* a, double sc) {
+        dw s = dw_from_double(sc);
+        return dw_to_double(dw_mulc(dw{a[0], a[1]}, s.h, s.l));
+    }
+};
+
+struct SmemS {
+    size_t xs, ws, cs, acc_e, acc_v, acc_g, acc_b, bmap, total;
+};
+
+template <int DIM, int PREC, int WHAT>
+__host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
+    using F = Form<PREC>;
+    using SC = Scat<PREC>;
+    SmemS s;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { o = (o + 15) & ~size_t(15); size_t r = o; o += bytes; return r; };
+    const size_t wb = sizeof(typename SC::S) * SC::W;
+    s.xs = take(sizeof(typename F::C) * DIM * D.max_nodes);
+    s.ws = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * DIM * D.max_edges) : 0;
+    s.cs = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * D.max_nodes) : 0;
+    s.acc_e = (WHAT & DO_FWD) ? take(wb * DIM * D.max_eo) : 0;
+    s.acc_v = (WHAT & DO_FWD) ? take(wb * D.max_own) : 0;
+    s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
+    s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
+    s.bmap = take(sizeof(int) * D.max_own);
+    s.total = (o + 15) & ~size_t(15);
+    return s;
+}
+
+template <int DIM, int PREC, int WHAT>
+__device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char* smem) {
+    using F = Form<PREC>;
+    using SC = Scat<PREC>;
+    using C = typename F::C;
+    using V = typename F::V;
+    using S = typename SC::S;
+    constexpr int WW = SC::W;
+    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
+    const TileInfo ti = plan_at<TileInfo>(A.plan, H->off_tiles)[t];
+    const ElemConn* conn = plan_at<ElemConn>(A.plan, H->off_conn) + ti.elem_off;
+    const ElemEdges* tedge = plan_at<ElemEdges>(A.plan, H->off_tedge) + ti.elem_off;
+    const int32_t* halo = plan_at<int32_t>(A.plan, H->off_halo) + ti.halo_off;
+    const int32_t* hedge = plan_at<int32_t>(A.plan, H->off_hedge) + ti.hedge_off;
+    const TileBFace* tbf = plan_at<TileBFace>(A.plan, H->off_tbf) + ti.bf_off;
+
+    const SmemS L = smem_layout_s<DIM, PREC, WHAT>(A.D);
+    C* xs = reinterpret_cast<C*>(smem + L.xs);
+    V* ws = reinterpret_cast<V*>(smem + L.ws);
+    V* cs = reinterpret_cast<V*>(smem + L.cs);
+    S* acc_e = reinterpret_cast<S*>(smem + L.acc_e);
+    S* acc_v = reinterpret_cast<S*>(smem + L.acc_v);
+    S* acc_g = reinterpret_cast<S*>(smem + L.acc_g);
+    S* acc_b = reinterpret_cast<S*>(smem + L.acc_b);
+    int* bmap = reinterpret_cast<int*>(smem + L.bmap);
+
+    const int tid = threadIdx.x;
+    const int nnodes = ti.n_own + ti.n_halo;
+    double org[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    for (int i = tid; i < nnodes; i += NT) {
+        int64_t v = i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]);
+#pragma unroll
+        for (int d = 0; d < DIM; d++) xs[i * DIM + d] = F::coord(A.x[v * DIM + d], org[d]);
+        if (WHAT & DO_ADJ) cs[i] = A.c ? F::from_double(A.c[v]) : F::cst(0.0);
+    }
+    if (WHAT & DO_ADJ) {
+        const int nte = ti.n_eo + ti.n_hedge;
+        for (int i = tid; i < nte; i += NT) {
+            int64_t e = i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]);
+#pragma unroll
+            for (int d = 0; d < DIM; d++) ws[i * DIM + d] = F::from_double(A.w[e * DIM + d]);
+        }
+    }
+    if (WHAT & DO_FWD) {
+        for (int q = tid; q < ti.n_eo * DIM; q += NT) SC::zero(acc_e + q * WW);
+        for (int q = tid; q < ti.n_own; q += NT) SC::zero(acc_v + q * WW);
+        for (int q = tid; q < ti.n_bo * DIM; q += NT) SC::zero(acc_b + q * WW);
+    }
+    if (WHAT & DO_ADJ)
+        for (int q = tid; q < ti.n_own * DIM; q += NT) SC::zero(acc_g + q * WW);
+    for (int i = tid; i < ti.n_own; i += NT) bmap[i] = -1;
+    __syncthreads();
+    for (int k = tid; k < ti.n_bo; k += NT) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
+    __syncthreads();
+
+    // ---- elements: compute and scatter to owned targets -------------------
+    for (int i = tid; i < ti.n_el; i += NT) {
+        const ElemConn cn = conn[i];
+        const ElemEdges ee = tedge[i];
+        if (DIM == 3) {
+            V a[3], b[3], c[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                a[d] = F::diff(xs[cn.v[1] * 3 + d], xs[cn.v[0] * 3 + d]);
+                b[d] = F::diff(xs[cn.v[2] * 3 + d], xs[cn.v[0] * 3 + d]);
+                c[d] = F::diff(xs[cn.v[3] * 3 + d], xs[cn.v[0] * 3 + d]);
+            }
+            V N1[3] = {F::det2(b[1], c[2], b[2], c[1]), F::det2(b[2], c[0], b[0], c[2]), F::det2(b[0], c[1], b[1], c[0])};
+            V N2[3] = {F::det2(c[1], a[2], c[2], a[1]), F::det2(c[2], a[0], c[0], a[2]), F::det2(c[0], a[1], c[1], a[0])};
+            V N3[3] = {F::det2(a[1], b[2], a[2], b[1]), F::det2(a[2], b[0], a[0], b[2]), F::det2(a[0], b[1], a[1], b[0])};
+            V det = F::add(F::add(F::mul(a[0], N1[0]), F::mul(a[1], N1[1])), F::mul(a[2], N1[2]));
+            const float s = F::sign_of(det);
+            if (WHAT & DO_FWD) {
+                // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const V m0 = F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s);
+                    const V m1 = F::sgn(N1[d], -s);
+                    const V m2 = F::sgn(N2[d], -s);
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        const int le = ee.e[q];
+                        if (le < ti.n_eo) SC::add(acc_e + (le * 3 + d) * WW, q < 3 ? m0 : (q < 5 ? m1 : m2));
+                    }
+                }
+                const V vd = F::sgn(det, s);
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+                    if (cn.v[r] < ti.n_own) SC::add(acc_v + cn.v[r] * WW, vd);
+            }
+            if (WHAT & DO_ADJ) {
+                V W0[3], W1[3], W2[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    W0[d] = F::add(F::add(ws[ee.e[0] * 3 + d], ws[ee.e[1] * 3 + d]), ws[ee.e[2] * 3 + d]);
+                    W1[d] = F::add(ws[ee.e[3] * 3 + d], ws[ee.e[4] * 3 + d]);
+                    W2[d] = ws[ee.e[5] * 3 + d];
+                }
+                V A1[3], A2[3], A3[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    A1[d] = F::sub(W1[d], W0[d]);
+                    A2[d] = F::sub(W2[d], W0[d]);
+                    A3[d] = F::sgn(W0[d], -1.f);
+                }
+                V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]]));
+                const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
+                V h = F::sgn(F::mul(Cs, f24), s);
+                const bool own0 = cn.v[0] < ti.n_own, own1 = cn.v[1] < ti.n_own, own2 = cn.v[2] < ti.n_own,
+                           own3 = cn.v[3] < ti.n_own;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+                    V ga = F::sub(F::det2(A2[d1], c[d2], A2[d2], c[d1]), F::det2(A3[d1], b[d2], A3[d2], b[d1]));
+                    V gb = F::sub(F::det2(A3[d1], a[d2], A3[d2], a[d1]), F::det2(A1[d1], c[d2], A1[d2], c[d1]));
+                    V gc = F::sub(F::det2(A1[d1], b[d2], A1[d2], b[d1]), F::det2(A2[d1], a[d2], A2[d2], a[d1]));
+                    const V g1 = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
+                    const V g2 = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
+                    const V g3 = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
+                    if (own1) SC::add(acc_g + (cn.v[1] * 3 + d) * WW, g1);
+                    if (own2) SC::add(acc_g + (cn.v[2] * 3 + d) * WW, g2);
+                    if (own3) SC::add(acc_g + (cn.v[3] * 3 + d) * WW, g3);
+                    if (own0) SC::add(acc_g + (cn.v[0] * 3 + d) * WW, F::sgn(F::add(F::add(g1, g2), g3), -1.f));
+                }
+            }
+        } else {
+            V a[2], b[2];
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                a[d] = F::diff(xs[cn.v[1] * 2 + d], xs[cn.v[0] * 2 + d]);
+                b[d] = F::diff(xs[cn.v[2] * 2 + d], xs[cn.v[0] * 2 + d]);
+            }
+            V det = F::det2(a[0], b[1], a[1], b[0]);
+            const float s = F::sign_of(det);
+            if (WHAT & DO_FWD) {
+                V n1[2] = {F::sgn(b[1], -s), F::sgn(b[0], s)};
+                V n2[2] = {F::sgn(a[1], s), F::sgn(a[0], -s)};
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    const V m0 = F::sgn(F::add(n1[d], n2[d]), -1.f);
+                    if (ee.e[0] < ti.n_eo) SC::add(acc_e + (ee.e[0] * 2 + d) * WW, m0);
+                    if (ee.e[1] < ti.n_eo) SC::add(acc_e + (ee.e[1] * 2 + d) * WW, m0);
+                    if (ee.e[2] < ti.n_eo) SC::add(acc_e + (ee.e[2] * 2 + d) * WW, n1[d]);
+                }
+                const V vd = F::sgn(det, s);
+#pragma unroll
+                for (int r = 0; r < 3; r++)
+                    if (cn.v[r] < ti.n_own) SC::add(acc_v + cn.v[r] * WW, vd);
+            }
+            if (WHAT & DO_ADJ) {
+                V W0[2], W1[2];
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    W0[d] = F::add(ws[ee.e[0] * 2 + d], ws[ee.e[1] * 2 + d]);
+                    W1[d] = ws[ee.e[2] * 2 + d];
+                }
+                V A1[2] = {F::sub(W1[0], W0[0]), F::sub(W1[1], W0[1])};
+                V A2[2] = {F::sgn(W0[0], -1.f), F::sgn(W0[1], -1.f)};
+                V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), cs[cn.v[2]]);
+                const V f3 = F::cst(1.0 / 3.0), f6 = F::cst(1.0 / 6.0);
+                V h = F::sgn(F::mul(Cs, f6), s);
+                V gax = F::add(F::sgn(F::mul(A2[1], f3), -s), F::mul(h, b[1]));
+                V gay = F::add(F::sgn(F::mul(A2[0], f3), s), F::sgn(F::mul(h, b[0]), -1.f));
+                V gbx = F::add(F::sgn(F::mul(A1[1], f3), s), F::sgn(F::mul(h, a[1]), -1.f));
+                V gby = F::add(F::sgn(F::mul(A1[0], f3), -s), F::mul(h, a[0]));
+                if (cn.v[1] < ti.n_own) { SC::add(acc_g + (cn.v[1] * 2) * WW, gax); SC::add(acc_g + (cn.v[1] * 2 + 1) * WW, gay); }
+                if (cn.v[2] < ti.n_own) { SC::add(acc_g + (cn.v[2] * 2) * WW, gbx); SC::add(acc_g + (cn.v[2] * 2 + 1) * WW, gby); }
+                if (cn.v[0] < ti.n_own) {
+                    SC::add(acc_g + (cn.v[0] * 2) * WW, F::sgn(F::add(gax, gbx), -1.f));
+                    SC::add(acc_g + (cn.v[0] * 2 + 1) * WW, F::sgn(F::add(gay, gby), -1.f));
+                }
+            }
+        }
+    }
+
+    // ---- boundary faces ------------------------------------------------------
+    for (int j = tid; j < ti.n_bf; j += NT) {
+        const TileBFace f = tbf[j];
+        if (DIM == 3) {
+            V u[3], tt[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                u[d] = F::diff(xs[f.v[1] * 3 + d], xs[f.v[0] * 3 + d]);
+                tt[d] = F::diff(xs[f.v[2] * 3 + d], xs[f.v[0] * 3 + d]);
+            }
+            if (WHAT & DO_FWD) {
+                V nB[3] = {F::half(F::det2(u[1], tt[2], u[2], tt[1])), F::half(F::det2(u[2], tt[0], u[0], tt[2])),
+                           F::half(F::det2(u[0], tt[1], u[1], tt[0]))};
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+#pragma unroll
+                    for (int q = 0; q < 3; q++)
+                        if (f.e[q] < ti.n_eo) SC::add(acc_e + (f.e[q] * 3 + d) * WW, nB[d]);
+#pragma unroll
+                    for (int q = 0; q < 3; q++)
+                        if (f.v[q] < ti.n_own && bmap[f.v[q]] >= 0) SC::add(acc_b + (bmap[f.v[q]] * 3 + d) * WW, nB[d]);
+                }
+            }
+            if (WHAT & DO_ADJ) {
+                V WB[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+                    WB[d] = F::add(F::add(ws[f.e[0] * 3 + d], ws[f.e[1] * 3 + d]), ws[f.e[2] * 3 + d]);
+                const V f24 = F::cst(1.0 / 24.0);
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+                    V gq = F::mul(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]), f24);
+                    V gr = F::mul(F::det2(WB[d1], u[d2], WB[d2], u[d1]), f24);
+                    if (f.v[1] < ti.n_own) SC::add(acc_g + (f.v[1] * 3 + d) * WW, gq);
+                    if (f.v[2] < ti.n_own) SC::add(acc_g + (f.v[2] * 3 + d) * WW, gr);
+                    if (f.v[0] < ti.n_own) SC::add(acc_g + (f.v[0] * 3 + d) * WW, F::sgn(F::add(gq, gr), -1.f));
+                }
+            }
+        } else {
+            if (WHAT & DO_FWD) {
+                V nB[2] = {F::diff(xs[f.v[0] * 2 + 1], xs[f.v[1] * 2 + 1]), F::diff(xs[f.v[1] * 2 + 0], xs[f.v[0] * 2 + 0])};
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    if (f.e[0] < ti.n_eo) SC::add(acc_e + (f.e[0] * 2 + d) * WW, F::half(nB[d]));
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        if (f.v[q] < ti.n_own && bmap[f.v[q]] >= 0) SC::add(acc_b + (bmap[f.v[q]] * 2 + d) * WW, nB[d]);
+                }
+            }
+            if (WHAT & DO_ADJ) {
+                const V f6 = F::cst(1.0 / 6.0);
+                V gx = F::mul(ws[f.e[0] * 2 + 1], f6);
+                V gy = F::sgn(F::mul(ws[f.e[0] * 2 + 0], f6), -1.f);
+                if (f.v[1] < ti.n_own) { SC::add(acc_g + (f.v[1] * 2) * WW, gx); SC::add(acc_g + (f.v[1] * 2 + 1) * WW, gy); }
+                if (f.v[0] < ti.n_own) {
+                    SC::add(acc_g + (f.v[0] * 2) * WW, F::sgn(gx, -1.f));
+                    SC::add(acc_g + (f.v[0] * 2 + 1) * WW, F::sgn(gy, -1.f));
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    const double esc = DIM == 3 ? 1.0 / 12.0 : 1.0 / 3.0;
+    const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
+    const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
+    if (WHAT & DO_FWD) {
+        for (int q = tid; q < ti.n_eo * DIM; q += NT) A.n_out[int64_t(ti.edge0) * DIM + q] = SC::out(acc_e + q * WW, esc);
+        for (int q = tid; q < ti.n_bo * DIM; q += NT) A.bnormal[int64_t(ti.bnode0) * DIM + q] = SC::out(acc_b + q * WW, bsc);
+        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = SC::out(acc_v + q * WW, vsc);
+    }
+    if (WHAT & DO_ADJ)
+        for (int q = tid; q < ti.n_own * DIM; q += NT) A.grad[int64_t(ti.node0) * DIM + q] = SC::out(acc_g + q * WW, 1.0);
+}
+
+template <int DIM, int PREC, int WHAT>
+__global__ void __launch_bounds__(NT) k_tile_scatter(TileArgs A) {
+    extern __shared__ __align__(16) char smem[];
+    run_tile_scatter<DIM, PREC, WHAT>(A, (int)(A.tile_base + blockIdx.x), smem);
+}
+
+template <int DIM, int PREC, int WHAT>
+int launch_tiles_scatter(const em_mesh* m, TileArgs& A, cudaStream_t s) {
+    const SmemS L = smem_layout_s<DIM, PREC, WHAT>(A.D);
+    static size_t configured = 0;
+    if (L.total > 227 * 1024)
+        return fail(EM_ERR_ARG, "tile needs " + std::to_string(L.total) +
+                                    " bytes of shared memory (> 227 KB): rebuild the plan with a smaller tile_nodes");
+    if (L.total > 48 * 1024 && L.total > configured) {
+        EM_CUDA_TRY(cudaFuncSetAttribute(k_tile_scatter<DIM, PREC, WHAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024));
+        configured = 227 * 1024;
+    }
+    const int64_t n_tiles = m->plan_info[EM_PLAN_INFO_TILES];
+    const int64_t chunk = 1 << 30;
+    for (int64_t base = 0; base < n_tiles; base += chunk) {
+        A.tile_base = base;
+        int64_t nb = n_tiles - base < chunk ? n_tiles - base : chunk;
+        k_tile_scatter<DIM, PREC, WHAT><<<(unsigned)nb, NT, L.total, s>>>(A);
+        note_launches(1);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
 template <int DIM, int PREC, int WHAT>
 __global__ void __launch_bounds__(NT) k_tile(TileArgs A) {
     extern __shared__ __align__(16) char smem[];
@@ -520,7 +928,7 @@ __global__ void __launch_bounds__(NT) k_tile(TileArgs A) {
 
 template <int DIM, int PREC, int WHAT>
 int launch_tiles(const em_mesh* m, TileArgs& A, cudaStream_t s) {
-    const Smem L = smem_layout<DIM, PREC, WHAT>(A.max_nodes, A.max_edges, A.max_eo, A.max_own, A.max_bo);
+    const Smem L = smem_layout<DIM, PREC, WHAT>(A.D);
     static size_t configured = 0;
     if (L.total > 227 * 1024)
         return fail(EM_ERR_ARG, "tile needs " + std::to_string(L.total) +
@@ -544,12 +952,110 @@ int launch_tiles(const em_mesh* m, TileArgs& A, cudaStream_t s) {
 
 template <int DIM, int PREC>
 int dispatch_what(const em_mesh* m, int what, TileArgs& A, cudaStream_t s) {
+    if (what & GATHER_SCATTER) {
+        const int w = what & (GATHER_FWD | GATHER_ADJ);
+        if (w == GATHER_FWD) return launch_tiles_scatter<DIM, PREC, DO_FWD>(m, A, s);
+        if (w == GATHER_ADJ) return launch_tiles_scatter<DIM, PREC, DO_ADJ>(m, A, s);
+        return launch_tiles_scatter<DIM, PREC, DO_FWD | DO_ADJ>(m, A, s);
+    }
     if (what == GATHER_FWD) return launch_tiles<DIM, PREC, DO_FWD>(m, A, s);
     if (what == GATHER_ADJ) return launch_tiles<DIM, PREC, DO_ADJ>(m, A, s);
     return launch_tiles<DIM, PREC, DO_FWD | DO_ADJ>(m, A, s);
 }
 
+// ---- batched: persistent blocks drain the tiles of many grids ---------------
+__device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs& A) {
+    A.plan = it.mesh.plan;
+    A.bnode = it.mesh.bnode;
+    A.x = it.x; A.w = it.w; A.c = it.c;
+    A.n_out = it.n_edge; A.vol = it.vol; A.bnormal = it.bnormal; A.grad = it.grad_x;
+    A.n_tiles = (int)it.mesh.plan_info[EM_PLAN_INFO_TILES];
+    A.tile_base = 0;
+}
+
+template <int DIM, int PREC>
+__global__ void __launch_bounds__(NT) k_batched(const em_batch_item* __restrict__ items, const int64_t* __restrict__ prefix,
+                                               int n_meshes, Dims D, unsigned long long* counter, int32_t* status) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ long long s_next;
+    const int64_t total = prefix[n_meshes];
+    for (;;) {
+        if (threadIdx.x == 0) s_next = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t wk = s_next;
+        __syncthreads();
+        if (wk >= total) break;
+        int lo = 0, hi = n_meshes - 1;           // last mesh whose prefix <= wk
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= wk) lo = mid; else hi = mid - 1;
+        }
+        const em_batch_item& it = items[lo];
+        if (it.mesh.dim != DIM) {
+            if (threadIdx.x == 0) atomicExch(status, EM_ERR_ARG);
+            continue;
+        }
+        TileArgs A;
+        args_from_mesh(it, A);
+        A.D = D;
+        run_tile<DIM, PREC, DO_FWD | DO_ADJ>(A, (int)(wk - prefix[lo]), smem);
+        __syncthreads();
+    }
+}
+
+template <int DIM, int PREC>
+int launch_batched(int n_meshes, const em_batch_item* items, const int64_t* prefix, const Dims& D, int blocks,
+                   unsigned long long* counter, int32_t* status, cudaStream_t s) {
+    const Smem L = smem_layout<DIM, PREC, DO_FWD | DO_ADJ>(D);
+    if (L.total > 227 * 1024)
+        return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(L.total) +
+                                    " bytes of shared memory (> 227 KB): use a smaller tile_nodes");
+    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    if (blocks <= 0) {
+        int per_sm = 0;
+        EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<DIM, PREC>, NT, L.total));
+        blocks = num_sms() * (per_sm > 0 ? per_sm : 1);
+    }
+    k_batched<DIM, PREC><<<blocks, NT, L.total, s>>>(items, prefix, n_meshes, D, counter, status);
+    note_launches(1);
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
 }  // namespace
+
+int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, const int64_t* max_info,
+                 int dim, int precision, int blocks, int32_t* status, void* ws, size_t* ws_bytes, cudaStream_t s) {
+    bool query;
+    EM_TRY(check_ws(ws, ws_bytes, 256, &query));
+    if (query) return EM_OK;
+    if (n_meshes <= 0 || !items || !tile_prefix || !max_info || !status)
+        return fail(EM_ERR_ARG, "batched call needs items, tile_prefix, max_info and status");
+    if (dim != 2 && dim != 3) return fail(EM_ERR_ARG, "dim must be 2 or 3");
+    if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
+        return fail(EM_ERR_ARG, "batched pass supports FP64, DW and MIXED");
+    Dims D;
+    D.max_nodes = (int)max_info[EM_PLAN_INFO_MAX_NODES];
+    D.max_edges = (int)max_info[EM_PLAN_INFO_MAX_EDGES];
+    D.max_eo = (int)max_info[EM_PLAN_INFO_MAX_OWNED_EDGES];
+    D.max_own = (int)max_info[EM_PLAN_INFO_MAX_OWNED_NODES];
+    D.max_bo = (int)max_info[EM_PLAN_INFO_MAX_OWNED_BNODES];
+    D.max_es = (int)max_info[EM_PLAN_INFO_MAX_ESLOTS];
+    D.max_ns = (int)max_info[EM_PLAN_INFO_MAX_NSLOTS];
+    D.max_bs = (int)max_info[EM_PLAN_INFO_MAX_BSLOTS];
+    if (D.max_own <= 0 || D.max_nodes <= 0) return fail(EM_ERR_ARG, "max_info is empty");
+    unsigned long long* counter = static_cast<unsigned long long*>(ws);
+    EM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    EM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+    if (dim == 3) {
+        if (precision == EM_PREC_FP64) return launch_batched<3, EM_PREC_FP64>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+        if (precision == EM_PREC_DW) return launch_batched<3, EM_PREC_DW>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+        return launch_batched<3, EM_PREC_MIXED>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+    }
+    if (precision == EM_PREC_FP64) return launch_batched<2, EM_PREC_FP64>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+    if (precision == EM_PREC_DW) return launch_batched<2, EM_PREC_DW>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+    return launch_batched<2, EM_PREC_MIXED>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+}
 
 size_t gather_ws_bytes(const em_mesh*) { return 0; }
 
@@ -565,11 +1071,14 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
     A.bnode = m->bnode;
     A.x = x; A.w = w; A.c = c;
     A.n_out = n; A.vol = vol; A.bnormal = bnormal; A.grad = g;
-    A.max_nodes = (int)pi[EM_PLAN_INFO_MAX_NODES];
-    A.max_edges = (int)pi[EM_PLAN_INFO_MAX_EDGES];
-    A.max_eo = (int)pi[EM_PLAN_INFO_MAX_OWNED_EDGES];
-    A.max_own = (int)pi[EM_PLAN_INFO_MAX_OWNED_NODES];
-    A.max_bo = (int)pi[EM_PLAN_INFO_MAX_OWNED_BNODES];
+    A.D.max_nodes = (int)pi[EM_PLAN_INFO_MAX_NODES];
+    A.D.max_edges = (int)pi[EM_PLAN_INFO_MAX_EDGES];
+    A.D.max_eo = (int)pi[EM_PLAN_INFO_MAX_OWNED_EDGES];
+    A.D.max_own = (int)pi[EM_PLAN_INFO_MAX_OWNED_NODES];
+    A.D.max_bo = (int)pi[EM_PLAN_INFO_MAX_OWNED_BNODES];
+    A.D.max_es = (int)pi[EM_PLAN_INFO_MAX_ESLOTS];
+    A.D.max_ns = (int)pi[EM_PLAN_INFO_MAX_NSLOTS];
+    A.D.max_bs = (int)pi[EM_PLAN_INFO_MAX_BSLOTS];
     A.n_tiles = (int)pi[EM_PLAN_INFO_TILES];
     A.tile_base = 0;
     if (m->dim == 3) {
