@@ -84,9 +84,10 @@ extern "C" {
                              ascending order; FP64 only); bit-reproducible */
 #define EM_PATH_TILED  3  /* same tiles as EM_PATH_GATHER, but each tile element adds
                              its contributions to the tile's accumulators with
-                             shared-memory atomics (compensated FP32 for DW/MIXED):
-                             fewer instructions and barriers; accurate to the same
-                             contract, last bits not reproducible run to run */
+                             shared-memory integer atomics on exact fixed-point
+                             values (per-tile power-of-two scale, ~2^-49 relative
+                             resolution): fewer instructions and barriers, and
+                             bit-reproducible run to run */
 
 int em_version(void);
 
@@ -164,6 +165,8 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
 #define EM_PLAN_INFO_MAX_ESLOTS 10  /* most gather slots of one tile's owned edges */
 #define EM_PLAN_INFO_MAX_NSLOTS 11  /* most gather slots of one tile's owned nodes */
 #define EM_PLAN_INFO_MAX_BSLOTS 12  /* most gather slots of one tile's boundary nodes */
+#define EM_PLAN_INFO_MAX_EDGE_VALENCE 13  /* most contributions to one edge (elements + boundary faces) */
+#define EM_PLAN_INFO_MAX_NODE_VALENCE 14  /* most elements around one node */
 
 /* em_plan_build -- tiled gather plan for EM_PATH_GATHER (run once per
  * connectivity, after em_edge_build).
@@ -256,6 +259,19 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path,
                           const double* x, const double* w, const double* c,
                           double* n_edge, double* vol, double* bnormal, double* grad_x,
                           void* ws, size_t* ws_bytes, void* stream);
+
+/* em_edge_volume -- the edge-based median-dual volume of Sec. 4.1,
+ *   V_j = 1/(2D) sum_{edges {j,k}} (x_k - x_j) . n_jk,
+ * from given lumped directed-area vectors n_edge [n_edges][dim] (for example
+ * em_edge_metrics' output).  On a grid whose boundary faces are flat through
+ * each of their nodes it equals the element-based volume, so it doubles as an
+ * independent check of n_edge.  One thread per node sums its edges in
+ * ascending edge id with explicitly rounded FP64 arithmetic, so the result is
+ * the same floating-point expression as a serial edge loop.  vol [n_nodes] is
+ * overwritten.  Needs only mesh->edges (and n_nodes, n_edges, dim); the
+ * node-to-edge lists are built in the workspace. */
+int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, double* vol,
+                   void* ws, size_t* ws_bytes, void* stream);
 
 /* em_check_elements -- validation: counts elements with a node id outside
  * [0,n_nodes), a repeated node, or zero measure (det == 0 in FP64).

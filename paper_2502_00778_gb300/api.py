@@ -243,6 +243,22 @@ def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", ou
     return n, v, b, g
 
 
+def edge_volume(topo: Topology, x, n_edge):
+    """Edge-based dual volume (Sec. 4.1) from lumped directed-area vectors."""
+    L = load()
+    _require_cuda(x, n_edge)
+    x = x.contiguous().to(torch.float64)
+    n_edge = n_edge.contiguous().to(torch.float64)
+    v = torch.empty(topo.n_nodes, dtype=torch.float64, device=x.device)
+    m, mr = _mesh_ref(topo)
+    wsb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    check(L.em_edge_volume(mr, _ptr(x), _ptr(n_edge), _ptr(v), null, ctypes.byref(wsb), _stream()))
+    ws = workspace.get(wsb.value, x.device)
+    check(L.em_edge_volume(mr, _ptr(x), _ptr(n_edge), _ptr(v), _ptr(ws), ctypes.byref(wsb), _stream()))
+    return v
+
+
 def check_elements(dim: int, elems: torch.Tensor, x: torch.Tensor):
     """(bad-id count, degenerate count); raises EMError on either."""
     L = load()
@@ -283,3 +299,83 @@ class EdgeMetrics(torch.autograd.Function):
         g = edge_metrics_adjoint(topo, x, gn, gv, ctx.precision if ctx.precision != "mixed_comp32" else "mixed",
                                  adj_path)
         return g, None, None, None
+
+
+class Batch:
+    """Forward + adjoint of many grids of uneven size in one persistent launch.
+
+    All device-side descriptions (the em_batch_item array, the tile prefix
+    sums, the outputs) are built once here and keep fixed addresses, so
+    run() only enqueues the library call and a captured CUDA graph of run()
+    can be replayed after the inputs (x, w, c) are updated in place.
+    """
+
+    def __init__(self, topos, xs, ws, cs, precision: str = "dw", blocks: int = 0):
+        L = load()
+        if not topos:
+            raise ValueError("empty batch")
+        self.dim = topos[0].dim
+        if any(t.dim != self.dim for t in topos):
+            raise ValueError("all grids of a batch must have the same dimension")
+        if any(t.plan is None for t in topos):
+            raise ValueError("every grid needs a plan (plan_build)")
+        dev = xs[0].device
+        self.topos, self.xs, self.ws, self.cs = topos, xs, ws, cs
+        self.precision = precision
+        self.blocks = blocks
+        self.outs = []
+        items = (_lib.EmBatchItem * len(topos))()
+        for i, (t, x, w, c) in enumerate(zip(topos, xs, ws, cs)):
+            d = t.dim
+            o = (torch.empty((t.n_edges, d), dtype=torch.float64, device=dev),
+                 torch.empty(t.n_nodes, dtype=torch.float64, device=dev),
+                 torch.empty((t.n_bnodes, d), dtype=torch.float64, device=dev),
+                 torch.empty((t.n_nodes, d), dtype=torch.float64, device=dev))
+            self.outs.append(o)
+            items[i].mesh = t.em_mesh()
+            items[i].x, items[i].w = x.data_ptr(), w.data_ptr()
+            items[i].c = c.data_ptr() if c is not None else None
+            items[i].n_edge, items[i].vol = o[0].data_ptr(), o[1].data_ptr()
+            items[i].bnormal, items[i].grad_x = o[2].data_ptr(), o[3].data_ptr()
+        raw = bytes(items)
+        self.items = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+        tiles = [t.plan_info[1] for t in topos]
+        prefix = [0]
+        for n in tiles:
+            prefix.append(prefix[-1] + n)
+        self.n_tiles = prefix[-1]
+        self.prefix = torch.tensor(prefix, dtype=torch.int64, device=dev)
+        self.max_info = (ctypes.c_int64 * 16)()
+        for t in topos:
+            for k, v in enumerate(t.plan_info):
+                self.max_info[k] = max(self.max_info[k], v)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        wsb = ctypes.c_size_t(0)
+        check(L.em_batched_fwd_adj(len(topos), None, None, self.max_info, self.dim, PREC[precision], blocks, None,
+                                   None, ctypes.byref(wsb), _stream()))
+        self.wsb = wsb.value
+        self.wsbuf = torch.empty(max(self.wsb, 256), dtype=torch.uint8, device=dev)
+
+    def run(self):
+        """Enqueue the batched launch on the current stream."""
+        wsb = ctypes.c_size_t(self.wsbuf.numel())
+        check(load().em_batched_fwd_adj(len(self.topos), _ptr(self.items), _ptr(self.prefix), self.max_info, self.dim,
+                                        PREC[self.precision], self.blocks, _ptr(self.status), _ptr(self.wsbuf),
+                                        ctypes.byref(wsb), _stream()))
+
+    def capture(self):
+        """A CUDA graph of run(); replay() it after updating the inputs in place."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        return g
+
+    def check_status(self):
+        st = int(self.status.item())
+        if st != 0:
+            raise _lib.EMError(st, "batched launch reported an item error")

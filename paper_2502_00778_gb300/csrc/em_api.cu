@@ -170,6 +170,19 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path, const do
     return st == EM_OK ? ok() : st;
 }
 
+int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, double* vol, void* ws,
+                   size_t* ws_bytes, void* stream) {
+    if (!mesh) return fail(EM_ERR_ARG, "mesh is NULL");
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(EM_ERR_ARG, "mesh->dim must be 2 or 3");
+    if (mesh->n_nodes <= 0 || mesh->n_edges <= 0 || !mesh->edges) return fail(EM_ERR_ARG, "mesh needs edges");
+    bool query;
+    EM_TRY(check_ws(ws, ws_bytes, edge_volume_ws_bytes(mesh), &query));
+    if (query) return ok();
+    if (!x || !n_edge || !vol) return fail(EM_ERR_ARG, "x, n_edge and vol must not be NULL");
+    int st = edge_volume(mesh, x, n_edge, vol, ws, as_stream(stream));
+    return st == EM_OK ? ok() : st;
+}
+
 int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems, const int32_t* elem2edge,
                   int64_t n_edges, const int32_t* edges, int64_t n_bfaces, const int32_t* bface,
                   const int32_t* bface_owner, int64_t n_bnodes, const int32_t* bnode, int tile_nodes, void* ws,

@@ -18,6 +18,7 @@
 //   dL/db = -(s/12)(A3 x a - A1 x c) + (C s/24) N2
 //   dL/dc = -(s/12)(A1 x b - A2 x a) + (C s/24) N3,  dL/dx_0 = -(sum).
 // In 2D n_1 = -s (b_y,-b_x), n_2 = -s (-a_y,a_x), factor 1/3, V_E/3 = |det|/6.
+
 #include "em_common.cuh"
 #include "em_kernels.cuh"
 
@@ -49,9 +50,9 @@ __device__ __forceinline__ f3 tof(d3 a) { return {(float)a.x, (float)a.y, (float
 // compensated FP32 atomic accumulation into (hi, lo)
 __device__ __forceinline__ void comp_add(float* hi, float* lo, float v) {
     float old = atomicAdd(hi, v);
-    float s = old + v;
-    float bb = s - old;
-    float err = (old - (s - bb)) + (v - bb);
+    float s = __fadd_rn(old, v);
+    float bb = __fsub_rn(s, old);
+    float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bb)), __fsub_rn(v, bb));
     atomicAdd(lo, err);
 }
 

@@ -232,6 +232,39 @@ __global__ void k_sort_lists(int64_t nkeys, const int64_t* __restrict__ off, int
     }
 }
 
+// edge-based volume (Sec. 4.1): node -> incident edges, ascending
+__global__ void k_edge_node_count(int64_t n_edges, const int32_t* __restrict__ edges, int32_t* __restrict__ cnt) {
+    GLOOP(e, n_edges) {
+        atomicAdd(&cnt[edges[2 * e]], 1);
+        atomicAdd(&cnt[edges[2 * e + 1]], 1);
+    }
+}
+__global__ void k_edge_node_fill(int64_t n_edges, const int32_t* __restrict__ edges, const int64_t* __restrict__ off,
+                                 int32_t* __restrict__ fill, int32_t* __restrict__ ent) {
+    GLOOP(e, n_edges) {
+        for (int a = 0; a < 2; a++) {
+            const int32_t v = edges[2 * e + a];
+            ent[off[v] + atomicAdd(&fill[v], 1)] = (int32_t)e;
+        }
+    }
+}
+template <int DIM>
+__global__ void k_edge_volume(int64_t nv, const int64_t* __restrict__ off, const int32_t* __restrict__ ent,
+                              const int32_t* __restrict__ edges, const double* __restrict__ x,
+                              const double* __restrict__ n, double* __restrict__ vol) {
+    GLOOP(i, nv) {
+        double acc = 0.0;
+        for (int64_t q = off[i]; q < off[i + 1]; q++) {
+            const int64_t e = ent[q];
+            const int64_t j = edges[2 * e], k = edges[2 * e + 1];
+            double sd = 0.0;
+            for (int c = 0; c < DIM; c++) sd = P(sd, M(S(x[DIM * k + c], x[DIM * j + c]), n[DIM * e + c]));
+            acc = P(acc, sd);
+        }
+        vol[i] = M(acc, 1.0 / (2.0 * DIM));
+    }
+}
+
 #undef GLOOP
 
 inline unsigned Gc(int64_t n) { return grid_for(n, NTC); }
@@ -264,7 +297,45 @@ CsrWs csr_layout(const em_mesh* m, void* ws, size_t* bytes) {
     return w;
 }
 
+struct EvWs {
+    int32_t *cnt, *fill, *ent;
+    int64_t* off;
+    void* scan;
+};
+EvWs ev_layout(const em_mesh* m, void* ws, size_t* bytes) {
+    WsLayout L(ws);
+    EvWs w;
+    w.cnt = L.take<int32_t>(m->n_nodes + 1);
+    w.fill = L.take<int32_t>(m->n_nodes + 1);
+    w.off = L.take<int64_t>(m->n_nodes + 1);
+    w.ent = L.take<int32_t>(2 * m->n_edges);
+    w.scan = L.take<char>(scan_ws_bytes(m->n_nodes + 1));
+    if (bytes) *bytes = L.bytes();
+    return w;
+}
+
 }  // namespace
+
+size_t edge_volume_ws_bytes(const em_mesh* m) {
+    size_t b = 0;
+    ev_layout(m, nullptr, &b);
+    return b;
+}
+
+int edge_volume(const em_mesh* m, const double* x, const double* n, double* vol, void* ws, cudaStream_t s) {
+    EvWs w = ev_layout(m, ws, nullptr);
+    EM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * (m->n_nodes + 1), s));
+    EM_CUDA_TRY(cudaMemsetAsync(w.fill, 0, 4 * (m->n_nodes + 1), s));
+    k_edge_node_count<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.cnt);
+    EM_TRY(exclusive_scan_i32_to_i64(w.cnt, w.off, m->n_nodes, w.scan, s));
+    k_edge_node_fill<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.off, w.fill, w.ent);
+    k_sort_lists<<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent);
+    if (m->dim == 3) k_edge_volume<3><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, x, n, vol);
+    else k_edge_volume<2><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, x, n, vol);
+    note_launches(4 + 3);
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
 
 size_t csr_fwd_ws_bytes(const em_mesh* m) {
     size_t b = 0;

@@ -11,6 +11,11 @@
 // Conversions between double and DW are done on the integer pipe (bit
 // manipulation), because FP32<->FP64 conversion instructions run on the slow
 // FP64 unit of this GPU.
+//
+// Every operation below is written with the round-to-nearest intrinsics
+// (__fadd_rn, __fsub_rn, __fmul_rn) or an explicit fmaf: the compiler never
+// fuses those into a multiply-add, whereas a plain "a*b - c" may be contracted
+// into one FMA, which silently breaks the error-free transformations.
 #pragma once
 #include <stdint.h>
 
@@ -21,26 +26,26 @@ struct dw {
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
-    s = a + b;
-    e = b - (s - a);
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
 __device__ __forceinline__ dw dw_neg(dw a) { return {-a.h, -a.l}; }
 
-// sign flip by a +-1.0f factor without a multiply-rounding question
-__device__ __forceinline__ dw dw_sgn(dw a, float s) { return {a.h * s, a.l * s}; }
+// sign flip by a +-1.0f factor (exact)
+__device__ __forceinline__ dw dw_sgn(dw a, float s) { return {__fmul_rn(a.h, s), __fmul_rn(a.l, s)}; }
 
 // a - b, renormalized (|l| <= ulp(h)/2 up to one rounding)
 __device__ __forceinline__ dw dw_sub_n(dw a, dw b) {
     float s, e;
     two_sum(a.h, -b.h, s, e);
-    e += a.l - b.l;
+    e = __fadd_rn(e, __fsub_rn(a.l, b.l));
     float r, q;
     fast_two_sum(s, e, r, q);
     return {r, q};
@@ -50,18 +55,18 @@ __device__ __forceinline__ dw dw_sub_n(dw a, dw b) {
 __device__ __forceinline__ dw dw_add(dw a, dw b) {
     float s, e;
     two_sum(a.h, b.h, s, e);
-    return {s, e + (a.l + b.l)};
+    return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
 }
 
 __device__ __forceinline__ dw dw_sub(dw a, dw b) {
     float s, e;
     two_sum(a.h, -b.h, s, e);
-    return {s, e + (a.l - b.l)};
+    return {s, __fadd_rn(e, __fsub_rn(a.l, b.l))};
 }
 
 // a * b (a.l * b.l dropped: below 2^-46 relative for renormalized inputs)
 __device__ __forceinline__ dw dw_mul(dw a, dw b) {
-    float p = a.h * b.h;
+    float p = __fmul_rn(a.h, b.h);
     float e = fmaf(a.h, b.h, -p);
     e = fmaf(a.h, b.l, e);
     e = fmaf(a.l, b.h, e);
@@ -70,7 +75,7 @@ __device__ __forceinline__ dw dw_mul(dw a, dw b) {
 
 // a * f for a float constant pair (fh + fl)
 __device__ __forceinline__ dw dw_mulc(dw a, float fh, float fl) {
-    float p = a.h * fh;
+    float p = __fmul_rn(a.h, fh);
     float e = fmaf(a.h, fh, -p);
     e = fmaf(a.h, fl, e);
     e = fmaf(a.l, fh, e);
@@ -80,13 +85,13 @@ __device__ __forceinline__ dw dw_mulc(dw a, float fh, float fl) {
 // p*q - r*s for DW inputs: the exact difference of the high products plus
 // first-order terms
 __device__ __forceinline__ dw dw_det2(dw p, dw q, dw r, dw s) {
-    float a = p.h * q.h;
-    float b = r.h * s.h;
+    float a = __fmul_rn(p.h, q.h);
+    float b = __fmul_rn(r.h, s.h);
     float ea = fmaf(p.h, q.h, -a);
     float eb = fmaf(r.h, s.h, -b);
     float h, t;
     two_sum(a, -b, h, t);
-    float lo = t + (ea - eb);
+    float lo = __fadd_rn(t, __fsub_rn(ea, eb));
     lo = fmaf(p.h, q.l, lo);
     lo = fmaf(p.l, q.h, lo);
     lo = fmaf(-r.h, s.l, lo);
@@ -98,14 +103,14 @@ __device__ __forceinline__ dw dw_det2(dw p, dw q, dw r, dw s) {
 __device__ __forceinline__ void dw_acc(dw& acc, dw v) {
     float s, e;
     two_sum(acc.h, v.h, s, e);
-    acc.l += e + v.l;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(e, v.l));
     acc.h = s;
 }
 
 __device__ __forceinline__ void dw_acc_f(dw& acc, float v) {
     float s, e;
     two_sum(acc.h, v, s, e);
-    acc.l += e;
+    acc.l = __fadd_rn(acc.l, e);
     acc.h = s;
 }
 
@@ -121,7 +126,7 @@ __device__ __forceinline__ dw dw_from_double(double d) {
     unsigned r = (unsigned)(b & 0x1fffffffu);
     int el = e - 1075 + 127;               // exponent of 2^(e - 1075)
     float lo = 0.f;
-    if (el > 0) lo = __uint2float_rn(r) * __uint_as_float((unsigned)el << 23);
+    if (el > 0) lo = __fmul_rn(__uint2float_rn(r), __uint_as_float((unsigned)el << 23));
     return {hi, sign ? -lo : lo};
 }
 
@@ -140,7 +145,7 @@ __device__ __forceinline__ double dw_to_double(dw a) {
     long long M = (1LL << 52) | ((long long)(sb & 0x7fffff) << 29);
     int k = 0;
     int sc = 306 - ex;                      // e * 2^(179 - ex): e in units of the double ulp of s
-    if (e != 0.f && sc > 0 && sc < 255) k = __float2int_rn(e * __uint_as_float((unsigned)sc << 23));
+    if (e != 0.f && sc > 0 && sc < 255) k = __float2int_rn(__fmul_rn(e, __uint_as_float((unsigned)sc << 23)));
     M += sign ? -(long long)k : (long long)k;
     long long E = ex - 127 + 1023;
     if (M >= (1LL << 53)) {

@@ -383,6 +383,10 @@ __global__ void k_tile_slot_max(int64_t n_tiles, const TileInfo* tiles, const in
     }
 }
 
+__global__ void k_max_run(const int32_t* ptr, int64_t n, int64_t* maxv) {
+    GRID_LOOP(i, n) atomicMax((unsigned long long*)maxv, (unsigned long long)(ptr[i + 1] - ptr[i]));
+}
+
 __global__ void k_key_counts(const uint64_t* k, int64_t n, int32_t* cnt) {
     GRID_LOOP(i, n) atomicAdd(&cnt[k[i]], 1);
 }
@@ -656,9 +660,15 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
 
     EM_CUDA_TRY(cudaMemsetAsync(smax, 0, 32, s));
     k_tile_slot_max<<<G(n_tiles), NT, 0, s>>>(n_tiles, tiles, eslot_ptr, nslot_ptr, nbn ? bslot_ptr : nullptr, smax);
+    k_max_run<<<G(n_edges), NT, 0, s>>>(eslot_ptr, n_edges, smax + 3);
+    int64_t* vmax = maxv + 7;
+    EM_CUDA_TRY(cudaMemsetAsync(vmax, 0, 8, s));
+    k_max_run<<<G(nv), NT, 0, s>>>(nslot_ptr, nv, vmax);
     // 8. header
     int64_t mx[8], sm[4];
+    int64_t node_val = 0;
     EM_CUDA_TRY(cudaMemcpyAsync(sm, smax, sizeof(sm), cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaMemcpyAsync(&node_val, vmax, 8, cudaMemcpyDeviceToHost, s));
     unsigned long long st[2];
     EM_CUDA_TRY(cudaMemcpyAsync(mx, maxv, sizeof(mx), cudaMemcpyDeviceToHost, s));
     EM_CUDA_TRY(cudaMemcpyAsync(st, status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -694,6 +704,8 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
         plan_info[EM_PLAN_INFO_MAX_ESLOTS] = sm[0];
         plan_info[EM_PLAN_INFO_MAX_NSLOTS] = sm[1];
         plan_info[EM_PLAN_INFO_MAX_BSLOTS] = sm[2];
+        plan_info[EM_PLAN_INFO_MAX_EDGE_VALENCE] = sm[3];
+        plan_info[EM_PLAN_INFO_MAX_NODE_VALENCE] = node_val;
     }
     return EM_OK;
 }

@@ -74,7 +74,7 @@ struct Form<EM_PREC_DW> {
     static __device__ __forceinline__ V mul(V a, V b) { return dw_mul(a, b); }
     static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return dw_det2(p, q, r, s); }
     static __device__ __forceinline__ V sgn(V a, float s) { return dw_sgn(a, s); }
-    static __device__ __forceinline__ V half(V a) { return {0.5f * a.h, 0.5f * a.l}; }
+    static __device__ __forceinline__ V half(V a) { return {__fmul_rn(0.5f, a.h), __fmul_rn(0.5f, a.l)}; }
     static __device__ __forceinline__ float sign_of(V a) { return (a.h > 0.f || (a.h == 0.f && a.l > 0.f)) ? 1.f : -1.f; }
     static __device__ __forceinline__ V from_double(double d) { return dw_from_double(d); }
     static __device__ __forceinline__ V cst(double d) { return dw_from_double(d); }
@@ -166,6 +166,7 @@ struct TileArgs {
     double* grad;
     Dims D;
     int n_tiles;
+    int val_e, val_v;          // largest edge / node valence of the grid
     int64_t tile_base;      // first tile handled by blockIdx.x == 0
 };
 
@@ -561,70 +562,125 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
 
 // ---------------------------------------------------------------------------
 // scatter mode: every tile element adds its contributions to the tile's owned
-// accumulators with shared-memory atomics (compensated: the rounding error of
-// each FP32 atomic add is recovered with TwoSum and added to a low word), so
-// no chunk barriers, staging buffers or gather lists are needed.  Accurate to
-// double-word level, but the summation order (hence the last bits) varies
-// from run to run.
+// accumulators with shared-memory atomics on EXACT fixed-point integers.  A
+// tile chooses, for each output kind, a power-of-two scale 2^sigma from its
+// own coordinate extent (and the largest |w|, |c| it stages) and the grid's
+// largest valences, such that no accumulated sum can leave the int64 range;
+// each contribution is rounded once to a multiple of 2^-sigma (about 2^-49
+// relative to the contributions' size) and summed exactly with two native
+// 32-bit integer atomics (low word, then high word plus carry).  Integer sums
+// do not depend on the order of the additions, so the results are
+// bit-reproducible, and no chunk barriers, staging buffers or gather lists
+// are needed.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void fx_add(unsigned* a, long long q) {
+    const unsigned lo = (unsigned)q;
+    const unsigned old = atomicAdd(a, lo);
+    const unsigned hi = (unsigned)((unsigned long long)q >> 32) + ((old + lo < old) ? 1u : 0u);
+    if (hi) atomicAdd(a + 1, hi);
+}
+
+__device__ __forceinline__ long long fx_load(const unsigned* a) {
+    return (long long)(((unsigned long long)a[1] << 32) | a[0]);
+}
+
+// 2^k as float / double, k in the normal range
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
+__device__ __forceinline__ double pow2d(int k) {
+    return __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
+}
+
+// scale exponent such that |sum| <= bound * 2^sigma < 2^61, clamped to
+// [-lim, lim] (a bound of 0 means every term is 0: any scale works)
+__device__ __forceinline__ int fx_sigma(double bound, int lim) {
+    if (!(bound > 0.0)) return 0;
+    const int e = (int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1023 + 1;   // bound < 2^e
+    const int sg = 61 - e;
+    return sg > lim ? lim : (sg < -lim ? -lim : sg);
+}
+
+// Magnitudes as order-preserving 32-bit keys: the upper word of |v| as an
+// IEEE double (exponent and 20 mantissa bits).  Non-negative doubles order
+// like their bit patterns, so an integer max gives the max magnitude, and
+// key_bound() returns a double >= every value with that key.  Integer pipe
+// only, and valid over the whole double range.
+__device__ __forceinline__ unsigned mkey(double v) {
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+}
+__device__ __forceinline__ double key_bound(unsigned k) {
+    return __longlong_as_double((long long)((unsigned long long)(k + 1u) << 32));
+}
+
 template <int PREC>
-struct Scat;
+struct Fix;
 
 template <>
-struct Scat<EM_PREC_FP64> {
-    using S = double;   // one shared word per accumulated component
-    static constexpr int W = 1;
-    static __device__ __forceinline__ void add(S* a, double v) { atomicAdd(a, v); }
-    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.0; }
-    static __device__ __forceinline__ double out(const S* a, double sc) { return a[0] * sc; }
+struct Fix<EM_PREC_FP64> {
+    static constexpr int LIM = 1000;
+    static __device__ __forceinline__ long long q(double v, int sg) { return __double2ll_rn(v * pow2d(sg)); }
+    static __device__ __forceinline__ unsigned mag(double v) { return mkey(v); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
+};
+
+// int64 -> double times a constant, without FP64 instructions
+__device__ __forceinline__ double fx_out_dw(long long q, int sg, double sc) {
+    if (q == 0) return 0.0;
+    const float hi = __ll2float_rn(q);
+    const long long r = q - __float2ll_rn(hi);
+    dw v{hi, __ll2float_rn(r)};
+    dw c = dw_from_double(sc);
+    double d = dw_to_double(dw_mulc(v, c.h, c.l));
+    // multiply by 2^-sg through the exponent field
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const long long ex = (long long)((b >> 52) & 0x7ff) - sg;
+    if (ex <= 0) return 0.0;
+    b = (b & ~(0x7ffULL << 52)) | ((unsigned long long)ex << 52);
+    return __longlong_as_double((long long)b);
+}
+
+template <>
+struct Fix<EM_PREC_DW> {
+    static __device__ __forceinline__ long long q(dw v, int sg) {
+        const float f = pow2f(sg);
+        return __float2ll_rn(__fmul_rn(v.h, f)) + __float2ll_rn(__fmul_rn(v.l, f));
+    }
+    static constexpr int LIM = 120;
+    static __device__ __forceinline__ unsigned mag(dw v) {
+        return mkey(f_to_double((fabsf(v.h) + fabsf(v.l)) * 1.000001f));
+    }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return fx_out_dw(q, sg, sc); }
 };
 
 template <>
-struct Scat<EM_PREC_DW> {
-    using S = float;    // (hi, lo) pairs
-    static constexpr int W = 2;
-    static __device__ __forceinline__ void add(S* a, dw v) {
-        const float old = atomicAdd(a, v.h);
-        float s, e;
-        two_sum(old, v.h, s, e);
-        atomicAdd(a + 1, e + v.l);
-    }
-    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.f; a[1] = 0.f; }
-    static __device__ __forceinline__ double out(const S* a, double sc) {
-        dw s = dw_from_double(sc);
-        return dw_to_double(dw_mulc(dw{a[0], a[1]}, s.h, s.l));
-    }
+struct Fix<EM_PREC_MIXED> {
+    static __device__ __forceinline__ long long q(float v, int sg) { return __float2ll_rn(__fmul_rn(v, pow2f(sg))); }
+    static constexpr int LIM = 120;
+    static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return fx_out_dw(q, sg, sc); }
 };
 
-template <>
-struct Scat<EM_PREC_MIXED> {
-    using S = float;
-    static constexpr int W = 2;
-    static __device__ __forceinline__ void add(S* a, float v) {
-        const float old = atomicAdd(a, v);
-        float s, e;
-        two_sum(old, v, s, e);
-        atomicAdd(a + 1, e);
-    }
-    static __device__ __forceinline__ void zero(S* a) { a[0] = 0.f; a[1] = 0.f; }
-    static __device__ __forceinline__ double out(const S* a, double sc) {
-        dw s = dw_from_double(sc);
-        return dw_to_double(dw_mulc(dw{a[0], a[1]}, s.h, s.l));
-    }
-};
+// key of an upper bound on |a - b| for two staged coordinates
+__device__ __forceinline__ unsigned emag(double a, double b) { return mkey(a - b); }
+__device__ __forceinline__ unsigned emag(dw a, dw b) {
+    return mkey(f_to_double((fabsf(__fsub_rn(a.h, b.h)) + fabsf(a.l) + fabsf(b.l)) * 1.000001f));
+}
+
+__device__ __forceinline__ void block_max(unsigned* slot, unsigned v) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, v);
+}
 
 struct SmemS {
-    size_t xs, ws, cs, acc_e, acc_v, acc_g, acc_b, bmap, total;
+    size_t xs, ws, cs, acc_e, acc_v, acc_g, acc_b, bmap, red, total;
 };
 
 template <int DIM, int PREC, int WHAT>
 __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     using F = Form<PREC>;
-    using SC = Scat<PREC>;
     SmemS s;
     size_t o = 0;
     auto take = [&](size_t bytes) { o = (o + 15) & ~size_t(15); size_t r = o; o += bytes; return r; };
-    const size_t wb = sizeof(typename SC::S) * SC::W;
+    const size_t wb = 2 * sizeof(unsigned);
     s.xs = take(sizeof(typename F::C) * DIM * D.max_nodes);
     s.ws = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * DIM * D.max_edges) : 0;
     s.cs = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * D.max_nodes) : 0;
@@ -633,6 +689,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
     s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
     s.bmap = take(sizeof(int) * D.max_own);
+    s.red = take(sizeof(unsigned) * 4);
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -640,11 +697,9 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
 template <int DIM, int PREC, int WHAT>
 __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char* smem) {
     using F = Form<PREC>;
-    using SC = Scat<PREC>;
+    using FX = Fix<PREC>;
     using C = typename F::C;
     using V = typename F::V;
-    using S = typename SC::S;
-    constexpr int WW = SC::W;
     const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
     const TileInfo ti = plan_at<TileInfo>(A.plan, H->off_tiles)[t];
     const ElemConn* conn = plan_at<ElemConn>(A.plan, H->off_conn) + ti.elem_off;
@@ -657,42 +712,98 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     C* xs = reinterpret_cast<C*>(smem + L.xs);
     V* ws = reinterpret_cast<V*>(smem + L.ws);
     V* cs = reinterpret_cast<V*>(smem + L.cs);
-    S* acc_e = reinterpret_cast<S*>(smem + L.acc_e);
-    S* acc_v = reinterpret_cast<S*>(smem + L.acc_v);
-    S* acc_g = reinterpret_cast<S*>(smem + L.acc_g);
-    S* acc_b = reinterpret_cast<S*>(smem + L.acc_b);
+    unsigned* acc_e = reinterpret_cast<unsigned*>(smem + L.acc_e);
+    unsigned* acc_v = reinterpret_cast<unsigned*>(smem + L.acc_v);
+    unsigned* acc_g = reinterpret_cast<unsigned*>(smem + L.acc_g);
+    unsigned* acc_b = reinterpret_cast<unsigned*>(smem + L.acc_b);
     int* bmap = reinterpret_cast<int*>(smem + L.bmap);
+    unsigned* red = reinterpret_cast<unsigned*>(smem + L.red);
 
     const int tid = threadIdx.x;
     const int nnodes = ti.n_own + ti.n_halo;
+
+    // ---- clear accumulators --------------------------------------------------
+    if (tid < 4) red[tid] = 0u;
+    if (WHAT & DO_FWD) {
+        for (int q = tid; q < 2 * ti.n_eo * DIM; q += NT) acc_e[q] = 0u;
+        for (int q = tid; q < 2 * ti.n_own; q += NT) acc_v[q] = 0u;
+        for (int q = tid; q < 2 * ti.n_bo * DIM; q += NT) acc_b[q] = 0u;
+    }
+    if (WHAT & DO_ADJ)
+        for (int q = tid; q < 2 * ti.n_own * DIM; q += NT) acc_g[q] = 0u;
+    for (int i = tid; i < ti.n_own; i += NT) bmap[i] = -1;
+    __syncthreads();
+
+    // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
     double org[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    unsigned wm = 0u, cm = 0u;
     for (int i = tid; i < nnodes; i += NT) {
         int64_t v = i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]);
 #pragma unroll
         for (int d = 0; d < DIM; d++) xs[i * DIM + d] = F::coord(A.x[v * DIM + d], org[d]);
-        if (WHAT & DO_ADJ) cs[i] = A.c ? F::from_double(A.c[v]) : F::cst(0.0);
+        if (WHAT & DO_ADJ) {
+            const V cv = A.c ? F::from_double(A.c[v]) : F::cst(0.0);
+            cs[i] = cv;
+            cm = max(cm, FX::mag(cv));
+        }
     }
     if (WHAT & DO_ADJ) {
         const int nte = ti.n_eo + ti.n_hedge;
         for (int i = tid; i < nte; i += NT) {
             int64_t e = i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]);
 #pragma unroll
-            for (int d = 0; d < DIM; d++) ws[i * DIM + d] = F::from_double(A.w[e * DIM + d]);
+            for (int d = 0; d < DIM; d++) {
+                const V wv = F::from_double(A.w[e * DIM + d]);
+                ws[i * DIM + d] = wv;
+                wm = max(wm, FX::mag(wv));
+            }
         }
     }
-    if (WHAT & DO_FWD) {
-        for (int q = tid; q < ti.n_eo * DIM; q += NT) SC::zero(acc_e + q * WW);
-        for (int q = tid; q < ti.n_own; q += NT) SC::zero(acc_v + q * WW);
-        for (int q = tid; q < ti.n_bo * DIM; q += NT) SC::zero(acc_b + q * WW);
-    }
-    if (WHAT & DO_ADJ)
-        for (int q = tid; q < ti.n_own * DIM; q += NT) SC::zero(acc_g + q * WW);
-    for (int i = tid; i < ti.n_own; i += NT) bmap[i] = -1;
-    __syncthreads();
     for (int k = tid; k < ti.n_bo; k += NT) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
+    if (WHAT & DO_ADJ) {
+        block_max(red + 1, wm);
+        block_max(red + 2, cm);
+    }
     __syncthreads();
+
+    // ---- element extent: Lx bounds every coordinate difference along an edge
+    // from local node 0 of a tile element; every face vector, volume and
+    // gradient term below is bounded by a power of Lx (edges not at node 0 and
+    // boundary-face edges by 2 Lx), so the scales follow the element size, not
+    // the extent of the tile
+    {
+        unsigned lm = 0u;
+        for (int i = tid; i < ti.n_el; i += NT) {
+            const ElemConn cn = conn[i];
+#pragma unroll
+            for (int r = 1; r <= DIM; r++)
+#pragma unroll
+                for (int d = 0; d < DIM; d++) lm = max(lm, emag(xs[cn.v[r] * DIM + d], xs[cn.v[0] * DIM + d]));
+        }
+        block_max(red + 0, lm);
+    }
+    __syncthreads();
+
+    // ---- scales: no accumulated sum can exceed bound * 2^sigma < 2^61 ---------
+    const double Lx = key_bound(red[0]);
+    const double Ke = (double)A.val_e, Kv = (double)A.val_v;
+    constexpr int LIM = FX::LIM;
+    int sg_e, sg_v, sg_b, sg_g = 0;
+    if (DIM == 3) {
+        // |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3, |n_B| <= 8 Lx^2
+        sg_e = fx_sigma(32.0 * Lx * Lx * Ke, LIM);
+        sg_v = fx_sigma(8.0 * Lx * Lx * Lx * Kv, LIM);
+        sg_b = fx_sigma(32.0 * Lx * Lx * Kv, LIM);   // up to 3 boundary faces per element at a node
+        if (WHAT & DO_ADJ)
+            sg_g = fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx) * 2.0 * Kv, LIM);
+    } else {
+        sg_e = fx_sigma(8.0 * Lx * Ke, LIM);
+        sg_v = fx_sigma(16.0 * Lx * Lx * Kv, LIM);
+        sg_b = fx_sigma(8.0 * Lx * Kv, LIM);
+        if (WHAT & DO_ADJ) sg_g = fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx) * 2.0 * Kv, LIM);
+    }
 
     // ---- elements: compute and scatter to owned targets -------------------
     for (int i = tid; i < ti.n_el; i += NT) {
@@ -715,19 +826,19 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const V m0 = F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s);
-                    const V m1 = F::sgn(N1[d], -s);
-                    const V m2 = F::sgn(N2[d], -s);
+                    const long long q0 = FX::q(F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s), sg_e);
+                    const long long q1 = FX::q(F::sgn(N1[d], -s), sg_e);
+                    const long long q2 = FX::q(F::sgn(N2[d], -s), sg_e);
 #pragma unroll
-                    for (int q = 0; q < 6; q++) {
-                        const int le = ee.e[q];
-                        if (le < ti.n_eo) SC::add(acc_e + (le * 3 + d) * WW, q < 3 ? m0 : (q < 5 ? m1 : m2));
+                    for (int k = 0; k < 6; k++) {
+                        const int le = ee.e[k];
+                        if (le < ti.n_eo) fx_add(acc_e + 2 * (le * 3 + d), k < 3 ? q0 : (k < 5 ? q1 : q2));
                     }
                 }
-                const V vd = F::sgn(det, s);
+                const long long qv = FX::q(F::sgn(det, s), sg_v);
 #pragma unroll
                 for (int r = 0; r < 4; r++)
-                    if (cn.v[r] < ti.n_own) SC::add(acc_v + cn.v[r] * WW, vd);
+                    if (cn.v[r] < ti.n_own) fx_add(acc_v + 2 * cn.v[r], qv);
             }
             if (WHAT & DO_ADJ) {
                 V W0[3], W1[3], W2[3];
@@ -747,8 +858,6 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]]));
                 const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
                 V h = F::sgn(F::mul(Cs, f24), s);
-                const bool own0 = cn.v[0] < ti.n_own, own1 = cn.v[1] < ti.n_own, own2 = cn.v[2] < ti.n_own,
-                           own3 = cn.v[3] < ti.n_own;
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
@@ -758,10 +867,11 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                     const V g1 = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
                     const V g2 = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
                     const V g3 = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
-                    if (own1) SC::add(acc_g + (cn.v[1] * 3 + d) * WW, g1);
-                    if (own2) SC::add(acc_g + (cn.v[2] * 3 + d) * WW, g2);
-                    if (own3) SC::add(acc_g + (cn.v[3] * 3 + d) * WW, g3);
-                    if (own0) SC::add(acc_g + (cn.v[0] * 3 + d) * WW, F::sgn(F::add(F::add(g1, g2), g3), -1.f));
+                    if (cn.v[1] < ti.n_own) fx_add(acc_g + 2 * (cn.v[1] * 3 + d), FX::q(g1, sg_g));
+                    if (cn.v[2] < ti.n_own) fx_add(acc_g + 2 * (cn.v[2] * 3 + d), FX::q(g2, sg_g));
+                    if (cn.v[3] < ti.n_own) fx_add(acc_g + 2 * (cn.v[3] * 3 + d), FX::q(g3, sg_g));
+                    if (cn.v[0] < ti.n_own)
+                        fx_add(acc_g + 2 * (cn.v[0] * 3 + d), FX::q(F::sgn(F::add(F::add(g1, g2), g3), -1.f), sg_g));
                 }
             }
         } else {
@@ -778,15 +888,16 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V n2[2] = {F::sgn(a[1], s), F::sgn(a[0], -s)};
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    const V m0 = F::sgn(F::add(n1[d], n2[d]), -1.f);
-                    if (ee.e[0] < ti.n_eo) SC::add(acc_e + (ee.e[0] * 2 + d) * WW, m0);
-                    if (ee.e[1] < ti.n_eo) SC::add(acc_e + (ee.e[1] * 2 + d) * WW, m0);
-                    if (ee.e[2] < ti.n_eo) SC::add(acc_e + (ee.e[2] * 2 + d) * WW, n1[d]);
+                    const long long q0 = FX::q(F::sgn(F::add(n1[d], n2[d]), -1.f), sg_e);
+                    const long long q1 = FX::q(n1[d], sg_e);
+                    if (ee.e[0] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[0] * 2 + d), q0);
+                    if (ee.e[1] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[1] * 2 + d), q0);
+                    if (ee.e[2] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[2] * 2 + d), q1);
                 }
-                const V vd = F::sgn(det, s);
+                const long long qv = FX::q(F::sgn(det, s), sg_v);
 #pragma unroll
                 for (int r = 0; r < 3; r++)
-                    if (cn.v[r] < ti.n_own) SC::add(acc_v + cn.v[r] * WW, vd);
+                    if (cn.v[r] < ti.n_own) fx_add(acc_v + 2 * cn.v[r], qv);
             }
             if (WHAT & DO_ADJ) {
                 V W0[2], W1[2];
@@ -804,11 +915,17 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V gay = F::add(F::sgn(F::mul(A2[0], f3), s), F::sgn(F::mul(h, b[0]), -1.f));
                 V gbx = F::add(F::sgn(F::mul(A1[1], f3), s), F::sgn(F::mul(h, a[1]), -1.f));
                 V gby = F::add(F::sgn(F::mul(A1[0], f3), -s), F::mul(h, a[0]));
-                if (cn.v[1] < ti.n_own) { SC::add(acc_g + (cn.v[1] * 2) * WW, gax); SC::add(acc_g + (cn.v[1] * 2 + 1) * WW, gay); }
-                if (cn.v[2] < ti.n_own) { SC::add(acc_g + (cn.v[2] * 2) * WW, gbx); SC::add(acc_g + (cn.v[2] * 2 + 1) * WW, gby); }
+                if (cn.v[1] < ti.n_own) {
+                    fx_add(acc_g + 2 * (cn.v[1] * 2), FX::q(gax, sg_g));
+                    fx_add(acc_g + 2 * (cn.v[1] * 2 + 1), FX::q(gay, sg_g));
+                }
+                if (cn.v[2] < ti.n_own) {
+                    fx_add(acc_g + 2 * (cn.v[2] * 2), FX::q(gbx, sg_g));
+                    fx_add(acc_g + 2 * (cn.v[2] * 2 + 1), FX::q(gby, sg_g));
+                }
                 if (cn.v[0] < ti.n_own) {
-                    SC::add(acc_g + (cn.v[0] * 2) * WW, F::sgn(F::add(gax, gbx), -1.f));
-                    SC::add(acc_g + (cn.v[0] * 2 + 1) * WW, F::sgn(F::add(gay, gby), -1.f));
+                    fx_add(acc_g + 2 * (cn.v[0] * 2), FX::q(F::sgn(F::add(gax, gbx), -1.f), sg_g));
+                    fx_add(acc_g + 2 * (cn.v[0] * 2 + 1), FX::q(F::sgn(F::add(gay, gby), -1.f), sg_g));
                 }
             }
         }
@@ -829,12 +946,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                            F::half(F::det2(u[0], tt[1], u[1], tt[0]))};
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
+                    const long long qe = FX::q(nB[d], sg_e), qb = FX::q(nB[d], sg_b);
 #pragma unroll
-                    for (int q = 0; q < 3; q++)
-                        if (f.e[q] < ti.n_eo) SC::add(acc_e + (f.e[q] * 3 + d) * WW, nB[d]);
+                    for (int k = 0; k < 3; k++)
+                        if (f.e[k] < ti.n_eo) fx_add(acc_e + 2 * (f.e[k] * 3 + d), qe);
 #pragma unroll
-                    for (int q = 0; q < 3; q++)
-                        if (f.v[q] < ti.n_own && bmap[f.v[q]] >= 0) SC::add(acc_b + (bmap[f.v[q]] * 3 + d) * WW, nB[d]);
+                    for (int k = 0; k < 3; k++)
+                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) fx_add(acc_b + 2 * (bmap[f.v[k]] * 3 + d), qb);
                 }
             }
             if (WHAT & DO_ADJ) {
@@ -848,9 +966,9 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                     V gq = F::mul(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]), f24);
                     V gr = F::mul(F::det2(WB[d1], u[d2], WB[d2], u[d1]), f24);
-                    if (f.v[1] < ti.n_own) SC::add(acc_g + (f.v[1] * 3 + d) * WW, gq);
-                    if (f.v[2] < ti.n_own) SC::add(acc_g + (f.v[2] * 3 + d) * WW, gr);
-                    if (f.v[0] < ti.n_own) SC::add(acc_g + (f.v[0] * 3 + d) * WW, F::sgn(F::add(gq, gr), -1.f));
+                    if (f.v[1] < ti.n_own) fx_add(acc_g + 2 * (f.v[1] * 3 + d), FX::q(gq, sg_g));
+                    if (f.v[2] < ti.n_own) fx_add(acc_g + 2 * (f.v[2] * 3 + d), FX::q(gr, sg_g));
+                    if (f.v[0] < ti.n_own) fx_add(acc_g + 2 * (f.v[0] * 3 + d), FX::q(F::sgn(F::add(gq, gr), -1.f), sg_g));
                 }
             }
         } else {
@@ -858,20 +976,24 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V nB[2] = {F::diff(xs[f.v[0] * 2 + 1], xs[f.v[1] * 2 + 1]), F::diff(xs[f.v[1] * 2 + 0], xs[f.v[0] * 2 + 0])};
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    if (f.e[0] < ti.n_eo) SC::add(acc_e + (f.e[0] * 2 + d) * WW, F::half(nB[d]));
+                    if (f.e[0] < ti.n_eo) fx_add(acc_e + 2 * (f.e[0] * 2 + d), FX::q(F::half(nB[d]), sg_e));
+                    const long long qb = FX::q(nB[d], sg_b);
 #pragma unroll
-                    for (int q = 0; q < 2; q++)
-                        if (f.v[q] < ti.n_own && bmap[f.v[q]] >= 0) SC::add(acc_b + (bmap[f.v[q]] * 2 + d) * WW, nB[d]);
+                    for (int k = 0; k < 2; k++)
+                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) fx_add(acc_b + 2 * (bmap[f.v[k]] * 2 + d), qb);
                 }
             }
             if (WHAT & DO_ADJ) {
                 const V f6 = F::cst(1.0 / 6.0);
                 V gx = F::mul(ws[f.e[0] * 2 + 1], f6);
                 V gy = F::sgn(F::mul(ws[f.e[0] * 2 + 0], f6), -1.f);
-                if (f.v[1] < ti.n_own) { SC::add(acc_g + (f.v[1] * 2) * WW, gx); SC::add(acc_g + (f.v[1] * 2 + 1) * WW, gy); }
+                if (f.v[1] < ti.n_own) {
+                    fx_add(acc_g + 2 * (f.v[1] * 2), FX::q(gx, sg_g));
+                    fx_add(acc_g + 2 * (f.v[1] * 2 + 1), FX::q(gy, sg_g));
+                }
                 if (f.v[0] < ti.n_own) {
-                    SC::add(acc_g + (f.v[0] * 2) * WW, F::sgn(gx, -1.f));
-                    SC::add(acc_g + (f.v[0] * 2 + 1) * WW, F::sgn(gy, -1.f));
+                    fx_add(acc_g + 2 * (f.v[0] * 2), FX::q(F::sgn(gx, -1.f), sg_g));
+                    fx_add(acc_g + 2 * (f.v[0] * 2 + 1), FX::q(F::sgn(gy, -1.f), sg_g));
                 }
             }
         }
@@ -882,12 +1004,15 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
     const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < ti.n_eo * DIM; q += NT) A.n_out[int64_t(ti.edge0) * DIM + q] = SC::out(acc_e + q * WW, esc);
-        for (int q = tid; q < ti.n_bo * DIM; q += NT) A.bnormal[int64_t(ti.bnode0) * DIM + q] = SC::out(acc_b + q * WW, bsc);
-        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = SC::out(acc_v + q * WW, vsc);
+        for (int q = tid; q < ti.n_eo * DIM; q += NT)
+            A.n_out[int64_t(ti.edge0) * DIM + q] = FX::out(fx_load(acc_e + 2 * q), sg_e, esc);
+        for (int q = tid; q < ti.n_bo * DIM; q += NT)
+            A.bnormal[int64_t(ti.bnode0) * DIM + q] = FX::out(fx_load(acc_b + 2 * q), sg_b, bsc);
+        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = FX::out(fx_load(acc_v + 2 * q), sg_v, vsc);
     }
     if (WHAT & DO_ADJ)
-        for (int q = tid; q < ti.n_own * DIM; q += NT) A.grad[int64_t(ti.node0) * DIM + q] = SC::out(acc_g + q * WW, 1.0);
+        for (int q = tid; q < ti.n_own * DIM; q += NT)
+            A.grad[int64_t(ti.node0) * DIM + q] = FX::out(fx_load(acc_g + 2 * q), sg_g, 1.0);
 }
 
 template <int DIM, int PREC, int WHAT>
@@ -970,6 +1095,8 @@ __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs
     A.x = it.x; A.w = it.w; A.c = it.c;
     A.n_out = it.n_edge; A.vol = it.vol; A.bnormal = it.bnormal; A.grad = it.grad_x;
     A.n_tiles = (int)it.mesh.plan_info[EM_PLAN_INFO_TILES];
+    A.val_e = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_EDGE_VALENCE];
+    A.val_v = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_NODE_VALENCE];
     A.tile_base = 0;
 }
 
@@ -1010,7 +1137,7 @@ int launch_batched(int n_meshes, const em_batch_item* items, const int64_t* pref
     if (L.total > 227 * 1024)
         return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(L.total) +
                                     " bytes of shared memory (> 227 KB): use a smaller tile_nodes");
-    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     if (blocks <= 0) {
         int per_sm = 0;
         EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<DIM, PREC>, NT, L.total));
@@ -1080,6 +1207,8 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
     A.D.max_ns = (int)pi[EM_PLAN_INFO_MAX_NSLOTS];
     A.D.max_bs = (int)pi[EM_PLAN_INFO_MAX_BSLOTS];
     A.n_tiles = (int)pi[EM_PLAN_INFO_TILES];
+    A.val_e = (int)(pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] : 64);
+    A.val_v = (int)(pi[EM_PLAN_INFO_MAX_NODE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_NODE_VALENCE] : 64);
     A.tile_base = 0;
     if (m->dim == 3) {
         if (prec == EM_PREC_FP64) return dispatch_what<3, EM_PREC_FP64>(m, what, A, s);

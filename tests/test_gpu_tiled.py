@@ -88,3 +88,15 @@ def test_tiled_mixed(name):
     assert np.abs(v.cpu().numpy() - rv).max() / h ** m.dim < 2e-6
     rg = oracle.adjoint(m.dim, m.x, m.elems, oracle_topo(name), w, c)
     assert np.abs(g.cpu().numpy() - rg).max() / np.abs(rg).max() < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "dw", "mixed"])
+def test_tiled_is_bit_reproducible(prec, name="kuhn48"):
+    from paper_2502_00778_gb300 import api
+    m, x, topo = _setup(name)
+    w, c = loss_weights(name)
+    wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
+    r1 = api.edge_metrics_fused(topo, x, wt, ct, prec, path="tiled")
+    r2 = api.edge_metrics_fused(topo, x, wt, ct, prec, path="tiled")
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
