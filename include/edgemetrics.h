@@ -284,6 +284,42 @@ int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* 
                       const double* x, void* ws, size_t* ws_bytes, int64_t* counts, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free forward                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed scratch array behind em_edge_metrics_noalloc: 64 MiB of
+ * device memory that every GPU which loads this library keeps reserved until
+ * the process exits. */
+#define EM_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
+
+/* em_edge_metrics_noalloc -- the forward outputs (n_edge, vol, bnormal, as
+ * em_edge_metrics with EM_PATH_ATOMIC and EM_PREC_MIXED_COMP32) for callers
+ * that cannot allocate device memory at call time: solver plug-ins and
+ * callbacks whose host application owns every byte of device memory through
+ * its own pool, processes running under a fixed device-memory cap, or code
+ * paths where a cudaMalloc could fail or stall.  The paper has no counterpart:
+ * this is a deployment variant of the compensated-FP32 atomic form.
+ *
+ * The two-float edge and node accumulators of that form live in a
+ * library-owned array of EM_NOALLOC_SCRATCH_BYTES instead of a caller
+ * workspace, so the call takes no workspace and never allocates (no
+ * cudaMalloc, no cudaFree, no allocating library routine).  Requirement:
+ * 4 * (2*dim*n_edges + 2*n_nodes) <= EM_NOALLOC_SCRATCH_BYTES, otherwise
+ * EM_ERR_ARG and nothing is enqueued.
+ *   - The first call on each device looks up the array's device address
+ *     (once per device, with that device current); make that first call
+ *     before any stream capture begins.
+ *   - The array is cleared on `stream` at the start of every call.  All calls
+ *     share it, so calls whose work overlaps on the GPU (different streams or
+ *     threads, same device) race and corrupt each other's results; serialize
+ *     them.
+ *   - n_edge, vol and bnormal must all be given.  Outputs match
+ *     em_edge_metrics(ATOMIC, MIXED_COMP32) to its rounding (atomic order
+ *     differs between runs). */
+int em_edge_metrics_noalloc(const em_mesh* mesh, const double* x,
+                            double* n_edge, double* vol, double* bnormal, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched meshes                                                            */
 /* ------------------------------------------------------------------------ */
 

@@ -183,6 +183,15 @@ int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, d
     return st == EM_OK ? ok() : st;
 }
 
+int em_edge_metrics_noalloc(const em_mesh* mesh, const double* x, double* n_edge, double* vol, double* bnormal,
+                            void* stream) {
+    EM_TRY(check_mesh(mesh));
+    if (!x || !n_edge || !vol || (mesh->n_bnodes && !bnormal))
+        return fail(EM_ERR_ARG, "x, n_edge, vol and bnormal must not be NULL");
+    int st = atomic_fwd_noalloc(mesh, x, n_edge, vol, bnormal, as_stream(stream));
+    return st == EM_OK ? ok() : st;
+}
+
 int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems, const int32_t* elem2edge,
                   int64_t n_edges, const int32_t* edges, int64_t n_bfaces, const int32_t* bface,
                   const int32_t* bface_owner, int64_t n_bnodes, const int32_t* bnode, int tile_nodes, void* ws,

@@ -18,6 +18,7 @@
 //   dL/db = -(s/12)(A3 x a - A1 x c) + (C s/24) N2
 //   dL/dc = -(s/12)(A1 x b - A2 x a) + (C s/24) N3,  dL/dx_0 = -(sum).
 // In 2D n_1 = -s (b_y,-b_x), n_2 = -s (-a_y,a_x), factor 1/3, V_E/3 = |det|/6.
+#include <mutex>
 
 #include "em_common.cuh"
 #include "em_kernels.cuh"
@@ -442,6 +443,77 @@ int atomic_adj(const em_mesh* m, int prec, const double* x, const double* w, con
         else
             k_bnd_adj_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
                                                                       m->elem2edge, x, w, g);
+        note_launches(1);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free form of the compensated-FP32 forward: the (hi, lo)
+// accumulators live in this file-scope device array instead of a caller
+// workspace.  Host code must not pass the symbol itself to a kernel (on the
+// host it names a stand-in object, not device memory): it looks up the
+// device address once per device with cudaGetSymbolAddress and passes that.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float g_noalloc_scratch[EM_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+namespace {
+std::mutex g_noalloc_mutex;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+int noalloc_scratch(float** out) {
+    int dev = 0;
+    EM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(EM_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(EM_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return EM_OK;
+}
+}  // namespace
+
+int atomic_fwd_noalloc(const em_mesh* m, const double* x, double* n, double* vol, double* bnormal, cudaStream_t s) {
+    const int dim = m->dim;
+    const size_t ne_f = size_t(m->n_edges) * dim, nv_f = size_t(m->n_nodes);
+    const size_t need = (2 * ne_f + 2 * nv_f) * sizeof(float);
+    if (need > EM_NOALLOC_SCRATCH_BYTES)
+        return fail(EM_ERR_ARG, "grid needs " + std::to_string(need) + " bytes of scratch; the allocation-free forward "
+                                "holds " + std::to_string((unsigned long long)EM_NOALLOC_SCRATCH_BYTES) +
+                                " (use em_edge_metrics with a workspace)");
+    float* base = nullptr;
+    EM_TRY(noalloc_scratch(&base));
+    float* nhi = base;
+    float* nlo = nhi + ne_f;
+    float* vhi = nlo + ne_f;
+    float* vlo = vhi + nv_f;
+    EM_CUDA_TRY(cudaMemsetAsync(base, 0, need, s));
+    EM_CUDA_TRY(cudaMemsetAsync(bnormal, 0, sizeof(double) * m->n_bnodes * dim, s));
+    const int T = 256;
+    const unsigned G = grid_for(m->n_elems, T, int64_t(num_sms()) * 16);
+    if (dim == 3)
+        k_fwd_atomic3<EM_PREC_MIXED_COMP32><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, n, nullptr, nhi, nlo,
+                                                            vhi, vlo);
+    else
+        k_fwd_atomic2<EM_PREC_MIXED_COMP32><<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, n, nullptr, nhi, nlo,
+                                                            vhi, vlo);
+    k_comp_finalize<<<grid_for(int64_t(ne_f), T), T, 0, s>>>(int64_t(ne_f), nhi, nlo, n);
+    k_comp_finalize<<<grid_for(int64_t(nv_f), T), T, 0, s>>>(int64_t(nv_f), vhi, vlo, vol);
+    note_launches(3);
+    if (m->n_bfaces) {
+        if (dim == 3)
+            k_bnd_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+        else
+            k_bnd_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
         note_launches(1);
     }
     EM_CUDA_TRY(cudaGetLastError());
