@@ -376,15 +376,23 @@ def run_ours(args):
     e2e_value = ws * m.n_elems / (e2e_ms * 1e-3)
 
     # ---- per-form comparison (same workload, separate short timings) ----
+    # fused forward + adjoint per path and form, then the forward alone
+    # ("fwd:" keys), each with its own algorithmic bytes and roofline fraction
     forms = {}
     if not args.no_forms and rank == 0:
         cand = [("atomic", "fp64"), ("atomic", "mixed"), ("csr", "fp64")]
         if have_gather:
             cand += [(p_, q_) for p_ in ("gather", "tiled") for q_ in ("fp64", "dw", "mixed")]
+        cand += [("fwd:" + p_, q_) for p_, q_ in (("atomic", "fp64"), ("atomic", "mixed"), ("csr", "fp64"))]
+        if have_gather:
+            cand += [("fwd:tiled", q_) for q_ in ("fp64", "dw", "mixed")]
+        fwd_bytes = algorithmic_bytes(m, topo, "fwd", path)
         for pth, pr in cand:
             try:
                 def fstep():
-                    if pth in ("gather", "tiled"):
+                    if pth.startswith("fwd:"):
+                        api.edge_metrics(topo, x, pr, pth[4:], out=outs[:3])
+                    elif pth in ("gather", "tiled"):
                         api.edge_metrics_fused(topo, x, w, c, pr, out=outs, path=pth)
                     elif pth == "csr":
                         api.edge_metrics(topo, x, pr, "csr", out=outs[:3])
@@ -403,8 +411,10 @@ def run_ours(args):
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms = a.elapsed_time(b) / reps
+                nb = fwd_bytes if pth.startswith("fwd:") else step_bytes
                 forms[f"{pth}/{pr}"] = {"ms_per_step": round(ms, 4), "elements_per_s": m.n_elems / (ms * 1e-3),
-                                        "algorithmic_GBs": step_bytes / (ms * 1e-3) / 1e9}
+                                        "algorithmic_GBs": nb / (ms * 1e-3) / 1e9,
+                                        "roofline_frac": nb / (ms * 1e-3) / 1e9 / peak}
             except Exception as ex:  # a form that is not built reports why
                 forms[f"{pth}/{pr}"] = {"unavailable": str(ex)[:120]}
 
