@@ -137,6 +137,10 @@ __global__ void k_count_bface(int dim, int64_t nbf, const int32_t* bface, int T,
 }
 
 // ---- pairs ------------------------------------------------------------------
+// key = tile << 4 | owned mask (bit r: the r-th smallest node of the element
+// belongs to the tile).  Sorting by it groups a tile's elements by which of
+// their nodes (and hence, by lower end, which of their edges) the tile owns,
+// so the threads of a warp mostly share one mask and skip the same outputs.
 __global__ void k_fill_pairs(int dim, int64_t ne, const int32_t* elems, int T, const int64_t* off, uint64_t* keys,
                              uint32_t* vals) {
     GRID_LOOP(E, ne) {
@@ -144,8 +148,17 @@ __global__ void k_fill_pairs(int dim, int64_t ne, const int32_t* elems, int T, c
         sorted_nodes(dim, ld_el(elems, E), v, pos);
         int nt = distinct_tiles(dim, v, T, t);
         int64_t o = off[E];
-        for (int a = 0; a < nt; a++) { keys[o + a] = (uint64_t)t[a]; vals[o + a] = (uint32_t)E; }
+        for (int a = 0; a < nt; a++) {
+            unsigned mask = 0;
+            for (int r = 0; r <= dim; r++)
+                if (v[r] / T == t[a]) mask |= 1u << r;
+            keys[o + a] = ((uint64_t)t[a] << 4) | mask;
+            vals[o + a] = (uint32_t)E;
+        }
     }
+}
+__global__ void k_key_drop_mask(int64_t n, uint64_t* keys) {
+    GRID_LOOP(i, n) keys[i] >>= 4;
 }
 
 __global__ void k_fill_bpairs(int dim, int64_t nbf, const int32_t* bface, int T, const int64_t* off, uint64_t* keys,
@@ -545,7 +558,7 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     const int bt = bits_for(std::max<int64_t>(n_tiles - 1, 1));
     const int bn = bits_for(nv - 1);
     const int be = bits_for(n_edges - 1);
-    if (bt + bn > 63 || bt + be > 63) return fail(EM_ERR_ARG, "grid too large for the tile keys");
+    if (bt + bn > 63 || bt + be > 63 || bt + 4 > 63) return fail(EM_ERR_ARG, "grid too large for the tile keys");
 
     if (*ws_bytes < full_bytes) {
         if (plan) return fail(EM_ERR_WORKSPACE, "plan workspace too small: need " + std::to_string(full_bytes));
@@ -558,7 +571,8 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
 
     // 1. pairs (tile, element), elements ascending inside a tile (stable sort)
     k_fill_pairs<<<G(ne), NT, 0, s>>>(dim, ne, elems, T, poff, pk, pv);
-    EM_TRY(radix_sort_pairs(pk, pv, kt, vt, P, bt, sort_ws, s));
+    EM_TRY(radix_sort_pairs(pk, pv, kt, vt, P, bt + 4, sort_ws, s));
+    k_key_drop_mask<<<G(P), NT, 0, s>>>(P, pk);
     EM_TRY(exclusive_scan_i32_to_i64(tile_cnt, el_off, n_tiles, scan_b, s));
 
     // 2. halo nodes and halo edges of every tile (sorted, unique)

@@ -563,25 +563,49 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
 // ---------------------------------------------------------------------------
 // scatter mode: every tile element adds its contributions to the tile's owned
 // accumulators with shared-memory atomics on EXACT fixed-point integers.  A
-// tile chooses, for each output kind, a power-of-two scale 2^sigma from its
-// own coordinate extent (and the largest |w|, |c| it stages) and the grid's
-// largest valences, such that no accumulated sum can leave the int64 range;
-// each contribution is rounded once to a multiple of 2^-sigma (about 2^-49
-// relative to the contributions' size) and summed exactly with two native
-// 32-bit integer atomics (low word, then high word plus carry).  Integer sums
-// do not depend on the order of the additions, so the results are
-// bit-reproducible, and no chunk barriers, staging buffers or gather lists
-// are needed.
+// tile chooses, for each output kind, a power-of-two scale 2^sigma from the
+// largest coordinate difference along its elements' edges (and the largest
+// |w|, |c| it stages) and the grid's largest valences, such that no
+// accumulated sum can reach 2^62 (2^41 for the FP32 form).  Each contribution
+// is rounded once to a multiple of 2^-sigma and split into signed 21-bit
+// limbs (units 2^42, 2^21, 1; the FP32 form uses the lower two), each summed
+// with a native 32-bit integer atomic into its own shared-memory plane.  A
+// limb plane holds up to 1023 contributions per entry without overflow, so
+// no carries are propagated; the planes are recombined into one int64 at the
+// end.  Integer sums do not depend on the order of the additions, so the
+// results are bit-reproducible.
+//
+// The float -> limb split uses the classical "magic number" rounding on the
+// FP32 pipe: adding 1.5*2^23 to a float t with |t| < 2^22 rounds it to an
+// integer held in the low mantissa bits, and t - round(t) is exact.  (A
+// float -> int64 conversion instruction would run on the FP64 pipe, which is
+// 50x slower than the FP32 pipe on this GPU.)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void fx_add(unsigned* a, long long q) {
-    const unsigned lo = (unsigned)q;
-    const unsigned old = atomicAdd(a, lo);
-    const unsigned hi = (unsigned)((unsigned long long)q >> 32) + ((old + lo < old) ? 1u : 0u);
-    if (hi) atomicAdd(a + 1, hi);
+struct Lq {
+    int a, b, c;   // value = a*2^42 + b*2^21 + c (in units of 2^-sigma)
+};
+
+constexpr float FX_MAGIC = 12582912.0f;   // 1.5 * 2^23
+
+__device__ __forceinline__ int fx_round(float t, float& rem) {
+    const float y = __fadd_rn(t, FX_MAGIC);
+    rem = __fsub_rn(t, __fsub_rn(y, FX_MAGIC));
+    return __float_as_int(y) - 0x4B400000;
 }
 
-__device__ __forceinline__ long long fx_load(const unsigned* a) {
-    return (long long)(((unsigned long long)a[1] << 32) | a[0]);
+template <int NL>
+__device__ __forceinline__ void acc_add(int* p, int stride, int i, const Lq& q) {
+    atomicAdd(p + i, q.a);
+    atomicAdd(p + stride + i, q.b);
+    if (NL == 3) atomicAdd(p + 2 * stride + i, q.c);
+}
+
+template <int NL>
+__device__ __forceinline__ long long acc_load(const int* p, int stride, int i) {
+    if (NL == 3)
+        return (long long)((unsigned long long)(long long)p[i] << 42) +
+               (long long)((unsigned long long)(long long)p[stride + i] << 21) + (long long)p[2 * stride + i];
+    return (long long)((unsigned long long)(long long)p[i] << 21) + (long long)p[stride + i];
 }
 
 // 2^k as float / double, k in the normal range
@@ -590,13 +614,13 @@ __device__ __forceinline__ double pow2d(int k) {
     return __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
 }
 
-// scale exponent such that |sum| <= bound * 2^sigma < 2^61, clamped to
-// [-lim, lim] (a bound of 0 means every term is 0: any scale works)
-__device__ __forceinline__ int fx_sigma(double bound, int lim) {
+// scale exponent such that |sum| <= bound * 2^sigma < 2^top, clamped to
+// [lo, hi] (a bound of 0 means every term is 0: any scale works)
+__device__ __forceinline__ int fx_sigma(double bound, int top, int lo, int hi) {
     if (!(bound > 0.0)) return 0;
     const int e = (int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1023 + 1;   // bound < 2^e
-    const int sg = 61 - e;
-    return sg > lim ? lim : (sg < -lim ? -lim : sg);
+    const int sg = top - e;
+    return sg > hi ? hi : (sg < lo ? lo : sg);
 }
 
 // Magnitudes as order-preserving 32-bit keys: the upper word of |v| as an
@@ -616,21 +640,43 @@ struct Fix;
 
 template <>
 struct Fix<EM_PREC_FP64> {
-    static constexpr int LIM = 1000;
-    static __device__ __forceinline__ long long q(double v, int sg) { return __double2ll_rn(v * pow2d(sg)); }
+    static constexpr int NL = 3, TOP = 62, LO = -900, HI = 900;
+    static __device__ __forceinline__ Lq q(double v, int sg) {
+        const long long z = __double2ll_rn(v * pow2d(sg));    // FP64 pipe: this form is FP64-bound anyway
+        return {(int)(z >> 42), (int)((z >> 21) & 0x1fffff), (int)(z & 0x1fffff)};
+    }
     static __device__ __forceinline__ unsigned mag(double v) { return mkey(v); }
     static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
 };
 
-// int64 -> double times a constant, without FP64 instructions
+// int64 * 2^-sg * sc -> double without FP64 instructions: the integer is cut
+// into a double-word (its top 24 bits and the next 24), scaled in double-word
+// arithmetic and rounded to double; 2^-sg is applied through the exponent
 __device__ __forceinline__ double fx_out_dw(long long q, int sg, double sc) {
     if (q == 0) return 0.0;
-    const float hi = __ll2float_rn(q);
-    const long long r = q - __float2ll_rn(hi);
-    dw v{hi, __ll2float_rn(r)};
-    dw c = dw_from_double(sc);
-    double d = dw_to_double(dw_mulc(v, c.h, c.l));
-    // multiply by 2^-sg through the exponent field
+    const unsigned long long m = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    const int e = 63 - __clzll((long long)m);            // 2^e <= m < 2^(e+1)
+    const int sh = e - 23;
+    unsigned hb;
+    unsigned long long rest = 0;
+    if (sh > 0) {
+        hb = (unsigned)(m >> sh);
+        rest = m - ((unsigned long long)hb << sh);
+    } else {
+        hb = (unsigned)(m << (-sh));
+    }
+    float h = __uint_as_float(((unsigned)(e + 127) << 23) | (hb & 0x7fffffu));
+    float l = 0.f;
+    if (rest) {
+        const int sl = sh > 24 ? sh - 24 : 0;                 // keep the top 24 bits of rest
+        l = __fmul_rn(__uint2float_rn((unsigned)(rest >> sl)), pow2f(sl));
+    }
+    if (q < 0) {
+        h = -h;
+        l = -l;
+    }
+    const dw c = dw_from_double(sc);
+    const double d = dw_to_double(dw_mulc(dw{h, l}, c.h, c.l));
     unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const long long ex = (long long)((b >> 52) & 0x7ff) - sg;
     if (ex <= 0) return 0.0;
@@ -640,11 +686,18 @@ __device__ __forceinline__ double fx_out_dw(long long q, int sg, double sc) {
 
 template <>
 struct Fix<EM_PREC_DW> {
-    static __device__ __forceinline__ long long q(dw v, int sg) {
-        const float f = pow2f(sg);
-        return __float2ll_rn(__fmul_rn(v.h, f)) + __float2ll_rn(__fmul_rn(v.l, f));
+    static constexpr int NL = 3, TOP = 62, LO = -60, HI = 120;
+    static __device__ __forceinline__ Lq q(dw v, int sg) {
+        float r;
+        const float th = __fmul_rn(v.h, pow2f(sg - 42));
+        const int a = fx_round(th, r);
+        const int b = fx_round(__fmul_rn(r, 2097152.0f), r);
+        const int c = fx_round(__fmul_rn(r, 2097152.0f), r);
+        const float tl = __fmul_rn(v.l, pow2f(sg - 21));
+        const int b2 = fx_round(tl, r);
+        const int c2 = fx_round(__fmul_rn(r, 2097152.0f), r);
+        return {a, b + b2, c + c2};
     }
-    static constexpr int LIM = 120;
     static __device__ __forceinline__ unsigned mag(dw v) {
         return mkey(f_to_double((fabsf(v.h) + fabsf(v.l)) * 1.000001f));
     }
@@ -653,8 +706,13 @@ struct Fix<EM_PREC_DW> {
 
 template <>
 struct Fix<EM_PREC_MIXED> {
-    static __device__ __forceinline__ long long q(float v, int sg) { return __float2ll_rn(__fmul_rn(v, pow2f(sg))); }
-    static constexpr int LIM = 120;
+    static constexpr int NL = 2, TOP = 41, LO = -80, HI = 120;
+    static __device__ __forceinline__ Lq q(float v, int sg) {
+        float r;
+        const int a = fx_round(__fmul_rn(v, pow2f(sg - 21)), r);
+        const int b = fx_round(__fmul_rn(r, 2097152.0f), r);
+        return {a, b, 0};
+    }
     static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
     static __device__ __forceinline__ double out(long long q, int sg, double sc) { return fx_out_dw(q, sg, sc); }
 };
@@ -680,7 +738,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     SmemS s;
     size_t o = 0;
     auto take = [&](size_t bytes) { o = (o + 15) & ~size_t(15); size_t r = o; o += bytes; return r; };
-    const size_t wb = 2 * sizeof(unsigned);
+    const size_t wb = Fix<PREC>::NL * sizeof(int);
     s.xs = take(sizeof(typename F::C) * DIM * D.max_nodes);
     s.ws = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * DIM * D.max_edges) : 0;
     s.cs = (WHAT & DO_ADJ) ? take(sizeof(typename F::V) * D.max_nodes) : 0;
@@ -689,7 +747,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
     s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
     s.bmap = take(sizeof(int) * D.max_own);
-    s.red = take(sizeof(unsigned) * 4);
+    s.red = take(sizeof(unsigned) * 12);
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -712,10 +770,12 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     C* xs = reinterpret_cast<C*>(smem + L.xs);
     V* ws = reinterpret_cast<V*>(smem + L.ws);
     V* cs = reinterpret_cast<V*>(smem + L.cs);
-    unsigned* acc_e = reinterpret_cast<unsigned*>(smem + L.acc_e);
-    unsigned* acc_v = reinterpret_cast<unsigned*>(smem + L.acc_v);
-    unsigned* acc_g = reinterpret_cast<unsigned*>(smem + L.acc_g);
-    unsigned* acc_b = reinterpret_cast<unsigned*>(smem + L.acc_b);
+    constexpr int NL = FX::NL;
+    int* acc_e = reinterpret_cast<int*>(smem + L.acc_e);
+    int* acc_v = reinterpret_cast<int*>(smem + L.acc_v);
+    int* acc_g = reinterpret_cast<int*>(smem + L.acc_g);
+    int* acc_b = reinterpret_cast<int*>(smem + L.acc_b);
+    const int se = DIM * A.D.max_eo, sv = A.D.max_own, sgs = DIM * A.D.max_own, sb = DIM * A.D.max_bo;
     int* bmap = reinterpret_cast<int*>(smem + L.bmap);
     unsigned* red = reinterpret_cast<unsigned*>(smem + L.red);
 
@@ -723,14 +783,14 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const int nnodes = ti.n_own + ti.n_halo;
 
     // ---- clear accumulators --------------------------------------------------
-    if (tid < 4) red[tid] = 0u;
+    if (tid < 12) red[tid] = 0u;
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < 2 * ti.n_eo * DIM; q += NT) acc_e[q] = 0u;
-        for (int q = tid; q < 2 * ti.n_own; q += NT) acc_v[q] = 0u;
-        for (int q = tid; q < 2 * ti.n_bo * DIM; q += NT) acc_b[q] = 0u;
+        for (int q = tid; q < NL * se; q += NT) acc_e[q] = 0;
+        for (int q = tid; q < NL * sv; q += NT) acc_v[q] = 0;
+        for (int q = tid; q < NL * sb; q += NT) acc_b[q] = 0;
     }
     if (WHAT & DO_ADJ)
-        for (int q = tid; q < 2 * ti.n_own * DIM; q += NT) acc_g[q] = 0u;
+        for (int q = tid; q < NL * sgs; q += NT) acc_g[q] = 0;
     for (int i = tid; i < ti.n_own; i += NT) bmap[i] = -1;
     __syncthreads();
 
@@ -738,26 +798,68 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     double org[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    // gathers are issued in batches of SB per thread so that several loads are
+    // in flight before the first one is used
+    constexpr int SB = 4;
     unsigned wm = 0u, cm = 0u;
-    for (int i = tid; i < nnodes; i += NT) {
-        int64_t v = i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]);
+    float xl = 0.f;   // largest |low part| of a staged coordinate (DW forms)
+    for (int i0 = tid; i0 < nnodes; i0 += SB * NT) {
+        int64_t v[SB];
 #pragma unroll
-        for (int d = 0; d < DIM; d++) xs[i * DIM + d] = F::coord(A.x[v * DIM + d], org[d]);
-        if (WHAT & DO_ADJ) {
-            const V cv = A.c ? F::from_double(A.c[v]) : F::cst(0.0);
-            cs[i] = cv;
-            cm = max(cm, FX::mag(cv));
+        for (int u = 0; u < SB; u++) {
+            const int i = i0 + u * NT;
+            v[u] = i >= nnodes ? -1 : (i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]));
+        }
+        double xv[SB][DIM], cv[SB];
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            if (v[u] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) xv[u][d] = A.x[v[u] * DIM + d];
+            if (WHAT & DO_ADJ) cv[u] = A.c ? A.c[v[u]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            if (v[u] < 0) continue;
+            const int i = i0 + u * NT;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const C xc = F::coord(xv[u][d], org[d]);
+                xs[i * DIM + d] = xc;
+                if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
+            }
+            if (WHAT & DO_ADJ) {
+                const V c1 = F::from_double(cv[u]);
+                cs[i] = c1;
+                cm = max(cm, FX::mag(c1));
+            }
         }
     }
     if (WHAT & DO_ADJ) {
         const int nte = ti.n_eo + ti.n_hedge;
-        for (int i = tid; i < nte; i += NT) {
-            int64_t e = i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]);
+        for (int i0 = tid; i0 < nte; i0 += SB * NT) {
+            int64_t e[SB];
 #pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const V wv = F::from_double(A.w[e * DIM + d]);
-                ws[i * DIM + d] = wv;
-                wm = max(wm, FX::mag(wv));
+            for (int u = 0; u < SB; u++) {
+                const int i = i0 + u * NT;
+                e[u] = i >= nte ? -1 : (i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]));
+            }
+            double wv[SB][DIM];
+#pragma unroll
+            for (int u = 0; u < SB; u++)
+                if (e[u] >= 0)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) wv[u][d] = A.w[e[u] * DIM + d];
+#pragma unroll
+            for (int u = 0; u < SB; u++) {
+                if (e[u] < 0) continue;
+                const int i = i0 + u * NT;
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const V w1 = F::from_double(wv[u][d]);
+                    ws[i * DIM + d] = w1;
+                    wm = max(wm, FX::mag(w1));
+                }
             }
         }
     }
@@ -766,6 +868,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
         block_max(red + 1, wm);
         block_max(red + 2, cm);
     }
+    if constexpr (PREC != EM_PREC_FP64) block_max(red + 3, mkey(f_to_double(xl)));
     __syncthreads();
 
     // ---- element extent: Lx bounds every coordinate difference along an edge
@@ -773,42 +876,88 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     // gradient term below is bounded by a power of Lx (edges not at node 0 and
     // boundary-face edges by 2 Lx), so the scales follow the element size, not
     // the extent of the tile
-    {
+    if constexpr (PREC == EM_PREC_FP64) {
         unsigned lm = 0u;
         for (int i = tid; i < ti.n_el; i += NT) {
             const ElemConn cn = conn[i];
 #pragma unroll
             for (int r = 1; r <= DIM; r++)
 #pragma unroll
-                for (int d = 0; d < DIM; d++) lm = max(lm, emag(xs[cn.v[r] * DIM + d], xs[cn.v[0] * DIM + d]));
+                for (int d = 0; d < DIM; d++) lm = max(lm, mkey(xs[cn.v[r] * DIM + d] - xs[cn.v[0] * DIM + d]));
         }
         block_max(red + 0, lm);
+    } else {
+        // high parts only: |a - b| <= |a.h - b.h| (1 + 2^-23) + 2 max|low part|
+        float lm = 0.f;
+        for (int i = tid; i < ti.n_el; i += NT) {
+            const ElemConn cn = conn[i];
+#pragma unroll
+            for (int r = 1; r <= DIM; r++)
+#pragma unroll
+                for (int d = 0; d < DIM; d++)
+                    lm = fmaxf(lm, fabsf(__fsub_rn(xs[cn.v[r] * DIM + d].h, xs[cn.v[0] * DIM + d].h)));
+        }
+        block_max(red + 0, mkey(f_to_double(lm)));
     }
     __syncthreads();
 
     // ---- scales: no accumulated sum can exceed bound * 2^sigma < 2^61 ---------
-    const double Lx = key_bound(red[0]);
-    const double Ke = (double)A.val_e, Kv = (double)A.val_v;
-    constexpr int LIM = FX::LIM;
-    int sg_e, sg_v, sg_b, sg_g = 0;
-    if (DIM == 3) {
-        // |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3, |n_B| <= 8 Lx^2
-        sg_e = fx_sigma(32.0 * Lx * Lx * Ke, LIM);
-        sg_v = fx_sigma(8.0 * Lx * Lx * Lx * Kv, LIM);
-        sg_b = fx_sigma(32.0 * Lx * Lx * Kv, LIM);   // up to 3 boundary faces per element at a node
-        if (WHAT & DO_ADJ)
-            sg_g = fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx) * 2.0 * Kv, LIM);
-    } else {
-        sg_e = fx_sigma(8.0 * Lx * Ke, LIM);
-        sg_v = fx_sigma(16.0 * Lx * Lx * Kv, LIM);
-        sg_b = fx_sigma(8.0 * Lx * Kv, LIM);
-        if (WHAT & DO_ADJ) sg_g = fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx) * 2.0 * Kv, LIM);
+    // one thread derives the scales (double arithmetic), the block reads them
+    int* sgv = reinterpret_cast<int*>(red + 4);
+    if (tid == 0) {
+        const double Lx = PREC == EM_PREC_FP64 ? key_bound(red[0])
+                                               : key_bound(red[0]) * (1.0 + 0x1p-20) + 2.0 * key_bound(red[3]);
+        const double Ke = (double)A.val_e, Kv = (double)A.val_v;
+        constexpr int T = FX::TOP, LO = FX::LO, HI = FX::HI;
+        if (DIM == 3) {
+            // |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3, |n_B| <= 8 Lx^2
+            sgv[0] = fx_sigma(32.0 * Lx * Lx * Ke, T, LO, HI);
+            sgv[1] = fx_sigma(8.0 * Lx * Lx * Lx * Kv, T, LO, HI);
+            sgv[2] = fx_sigma(32.0 * Lx * Lx * Kv, T, LO, HI);   // up to 3 boundary faces per element at a node
+            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx) *
+                                                    2.0 * Kv, T, LO, HI)
+                                     : 0;
+        } else {
+            sgv[0] = fx_sigma(8.0 * Lx * Ke, T, LO, HI);
+            sgv[1] = fx_sigma(16.0 * Lx * Lx * Kv, T, LO, HI);
+            sgv[2] = fx_sigma(8.0 * Lx * Kv, T, LO, HI);
+            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx) * 2.0 * Kv, T,
+                                                LO, HI)
+                                     : 0;
+        }
     }
+    __syncthreads();
+    const int sg_e = sgv[0], sg_v = sgv[1], sg_b = sgv[2], sg_g = sgv[3];
 
     // ---- elements: compute and scatter to owned targets -------------------
-    for (int i = tid; i < ti.n_el; i += NT) {
-        const ElemConn cn = conn[i];
-        const ElemEdges ee = tedge[i];
+    // warps take chunks of 32 consecutive elements from a shared counter (the
+    // elements are grouped by owned mask, so work per chunk varies); the next
+    // chunk's records are loaded while the current one is computed
+    const int lane = tid & 31;
+    unsigned* chunk_ctr = red + 8;
+    auto grab = [&]() {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(chunk_ctr, 32u);
+        return __shfl_sync(0xffffffffu, b, 0);
+    };
+    int cur = grab();
+    ElemConn cn_nx{};
+    ElemEdges ee_nx{};
+    if (cur + lane < ti.n_el) {
+        cn_nx = conn[cur + lane];
+        ee_nx = tedge[cur + lane];
+    }
+    while (cur < ti.n_el) {
+        const int nxt = grab();
+        const int i = cur + lane;
+        const ElemConn cn = cn_nx;
+        const ElemEdges ee = ee_nx;
+        if (nxt + lane < ti.n_el) {
+            cn_nx = conn[nxt + lane];
+            ee_nx = tedge[nxt + lane];
+        }
+        cur = nxt;
+        if (i >= ti.n_el) continue;
         if (DIM == 3) {
             V a[3], b[3], c[3];
 #pragma unroll
@@ -822,23 +971,38 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             V N3[3] = {F::det2(a[1], b[2], a[2], b[1]), F::det2(a[2], b[0], a[0], b[2]), F::det2(a[0], b[1], a[1], b[0])};
             V det = F::add(F::add(F::mul(a[0], N1[0]), F::mul(a[1], N1[1])), F::mul(a[2], N1[2]));
             const float s = F::sign_of(det);
+            // ownership of the sorted nodes; edges are owned by their lower end,
+            // so edges (0,1),(0,2),(0,3) are owned iff node 0 is, (1,2),(1,3)
+            // iff node 1 is, (2,3) iff node 2 is.  Tile elements are grouped by
+            // this mask, so the branches below are warp-uniform almost always.
+            const bool o0 = cn.v[0] < ti.n_own, o1 = cn.v[1] < ti.n_own, o2 = cn.v[2] < ti.n_own,
+                       o3 = cn.v[3] < ti.n_own;
             if (WHAT & DO_FWD) {
                 // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const long long q0 = FX::q(F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s), sg_e);
-                    const long long q1 = FX::q(F::sgn(N1[d], -s), sg_e);
-                    const long long q2 = FX::q(F::sgn(N2[d], -s), sg_e);
+                    if (o0) {
+                        const Lq q0 = FX::q(F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s), sg_e);
 #pragma unroll
-                    for (int k = 0; k < 6; k++) {
-                        const int le = ee.e[k];
-                        if (le < ti.n_eo) fx_add(acc_e + 2 * (le * 3 + d), k < 3 ? q0 : (k < 5 ? q1 : q2));
+                        for (int k = 0; k < 3; k++)
+                            if (ee.e[k] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[k] * 3 + d, q0);
+                    }
+                    if (o1) {
+                        const Lq q1 = FX::q(F::sgn(N1[d], -s), sg_e);
+#pragma unroll
+                        for (int k = 3; k < 5; k++)
+                            if (ee.e[k] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[k] * 3 + d, q1);
+                    }
+                    if (o2) {
+                        const Lq q2 = FX::q(F::sgn(N2[d], -s), sg_e);
+                        if (ee.e[5] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[5] * 3 + d, q2);
                     }
                 }
-                const long long qv = FX::q(F::sgn(det, s), sg_v);
-#pragma unroll
-                for (int r = 0; r < 4; r++)
-                    if (cn.v[r] < ti.n_own) fx_add(acc_v + 2 * cn.v[r], qv);
+                const Lq qv = FX::q(F::sgn(det, s), sg_v);
+                if (o0) acc_add<NL>(acc_v, sv, cn.v[0], qv);
+                if (o1) acc_add<NL>(acc_v, sv, cn.v[1], qv);
+                if (o2) acc_add<NL>(acc_v, sv, cn.v[2], qv);
+                if (o3) acc_add<NL>(acc_v, sv, cn.v[3], qv);
             }
             if (WHAT & DO_ADJ) {
                 V W0[3], W1[3], W2[3];
@@ -858,20 +1022,28 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]]));
                 const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
                 V h = F::sgn(F::mul(Cs, f24), s);
+                // g_i is needed for owned node i, and all three for node 0
+                const bool na = o0 || o1, nb = o0 || o2, nc = o0 || o3;
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                    V ga = F::sub(F::det2(A2[d1], c[d2], A2[d2], c[d1]), F::det2(A3[d1], b[d2], A3[d2], b[d1]));
-                    V gb = F::sub(F::det2(A3[d1], a[d2], A3[d2], a[d1]), F::det2(A1[d1], c[d2], A1[d2], c[d1]));
-                    V gc = F::sub(F::det2(A1[d1], b[d2], A1[d2], b[d1]), F::det2(A2[d1], a[d2], A2[d2], a[d1]));
-                    const V g1 = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
-                    const V g2 = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
-                    const V g3 = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
-                    if (cn.v[1] < ti.n_own) fx_add(acc_g + 2 * (cn.v[1] * 3 + d), FX::q(g1, sg_g));
-                    if (cn.v[2] < ti.n_own) fx_add(acc_g + 2 * (cn.v[2] * 3 + d), FX::q(g2, sg_g));
-                    if (cn.v[3] < ti.n_own) fx_add(acc_g + 2 * (cn.v[3] * 3 + d), FX::q(g3, sg_g));
-                    if (cn.v[0] < ti.n_own)
-                        fx_add(acc_g + 2 * (cn.v[0] * 3 + d), FX::q(F::sgn(F::add(F::add(g1, g2), g3), -1.f), sg_g));
+                    V g1 = F::cst(0.0), g2 = F::cst(0.0), g3 = F::cst(0.0);
+                    if (na) {
+                        V ga = F::sub(F::det2(A2[d1], c[d2], A2[d2], c[d1]), F::det2(A3[d1], b[d2], A3[d2], b[d1]));
+                        g1 = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
+                    }
+                    if (nb) {
+                        V gb = F::sub(F::det2(A3[d1], a[d2], A3[d2], a[d1]), F::det2(A1[d1], c[d2], A1[d2], c[d1]));
+                        g2 = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
+                    }
+                    if (nc) {
+                        V gc = F::sub(F::det2(A1[d1], b[d2], A1[d2], b[d1]), F::det2(A2[d1], a[d2], A2[d2], a[d1]));
+                        g3 = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
+                    }
+                    if (o1) acc_add<NL>(acc_g, sgs, cn.v[1] * 3 + d, FX::q(g1, sg_g));
+                    if (o2) acc_add<NL>(acc_g, sgs, cn.v[2] * 3 + d, FX::q(g2, sg_g));
+                    if (o3) acc_add<NL>(acc_g, sgs, cn.v[3] * 3 + d, FX::q(g3, sg_g));
+                    if (o0) acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d, FX::q(F::sgn(F::add(F::add(g1, g2), g3), -1.f), sg_g));
                 }
             }
         } else {
@@ -883,21 +1055,27 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             }
             V det = F::det2(a[0], b[1], a[1], b[0]);
             const float s = F::sign_of(det);
+            // edges (0,1),(0,2) are owned iff node 0 is, (1,2) iff node 1 is
+            const bool o0 = cn.v[0] < ti.n_own, o1 = cn.v[1] < ti.n_own, o2 = cn.v[2] < ti.n_own;
             if (WHAT & DO_FWD) {
                 V n1[2] = {F::sgn(b[1], -s), F::sgn(b[0], s)};
                 V n2[2] = {F::sgn(a[1], s), F::sgn(a[0], -s)};
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    const long long q0 = FX::q(F::sgn(F::add(n1[d], n2[d]), -1.f), sg_e);
-                    const long long q1 = FX::q(n1[d], sg_e);
-                    if (ee.e[0] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[0] * 2 + d), q0);
-                    if (ee.e[1] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[1] * 2 + d), q0);
-                    if (ee.e[2] < ti.n_eo) fx_add(acc_e + 2 * (ee.e[2] * 2 + d), q1);
+                    if (o0) {
+                        const Lq q0 = FX::q(F::sgn(F::add(n1[d], n2[d]), -1.f), sg_e);
+                        if (ee.e[0] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[0] * 2 + d, q0);
+                        if (ee.e[1] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[1] * 2 + d, q0);
+                    }
+                    if (o1) {
+                        const Lq q1 = FX::q(n1[d], sg_e);
+                        if (ee.e[2] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[2] * 2 + d, q1);
+                    }
                 }
-                const long long qv = FX::q(F::sgn(det, s), sg_v);
-#pragma unroll
-                for (int r = 0; r < 3; r++)
-                    if (cn.v[r] < ti.n_own) fx_add(acc_v + 2 * cn.v[r], qv);
+                const Lq qv = FX::q(F::sgn(det, s), sg_v);
+                if (o0) acc_add<NL>(acc_v, sv, cn.v[0], qv);
+                if (o1) acc_add<NL>(acc_v, sv, cn.v[1], qv);
+                if (o2) acc_add<NL>(acc_v, sv, cn.v[2], qv);
             }
             if (WHAT & DO_ADJ) {
                 V W0[2], W1[2];
@@ -911,21 +1089,26 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), cs[cn.v[2]]);
                 const V f3 = F::cst(1.0 / 3.0), f6 = F::cst(1.0 / 6.0);
                 V h = F::sgn(F::mul(Cs, f6), s);
-                V gax = F::add(F::sgn(F::mul(A2[1], f3), -s), F::mul(h, b[1]));
-                V gay = F::add(F::sgn(F::mul(A2[0], f3), s), F::sgn(F::mul(h, b[0]), -1.f));
-                V gbx = F::add(F::sgn(F::mul(A1[1], f3), s), F::sgn(F::mul(h, a[1]), -1.f));
-                V gby = F::add(F::sgn(F::mul(A1[0], f3), -s), F::mul(h, a[0]));
-                if (cn.v[1] < ti.n_own) {
-                    fx_add(acc_g + 2 * (cn.v[1] * 2), FX::q(gax, sg_g));
-                    fx_add(acc_g + 2 * (cn.v[1] * 2 + 1), FX::q(gay, sg_g));
+                V gax = F::cst(0.0), gay = F::cst(0.0), gbx = F::cst(0.0), gby = F::cst(0.0);
+                if (o0 || o1) {
+                    gax = F::add(F::sgn(F::mul(A2[1], f3), -s), F::mul(h, b[1]));
+                    gay = F::add(F::sgn(F::mul(A2[0], f3), s), F::sgn(F::mul(h, b[0]), -1.f));
                 }
-                if (cn.v[2] < ti.n_own) {
-                    fx_add(acc_g + 2 * (cn.v[2] * 2), FX::q(gbx, sg_g));
-                    fx_add(acc_g + 2 * (cn.v[2] * 2 + 1), FX::q(gby, sg_g));
+                if (o0 || o2) {
+                    gbx = F::add(F::sgn(F::mul(A1[1], f3), s), F::sgn(F::mul(h, a[1]), -1.f));
+                    gby = F::add(F::sgn(F::mul(A1[0], f3), -s), F::mul(h, a[0]));
                 }
-                if (cn.v[0] < ti.n_own) {
-                    fx_add(acc_g + 2 * (cn.v[0] * 2), FX::q(F::sgn(F::add(gax, gbx), -1.f), sg_g));
-                    fx_add(acc_g + 2 * (cn.v[0] * 2 + 1), FX::q(F::sgn(F::add(gay, gby), -1.f), sg_g));
+                if (o1) {
+                    acc_add<NL>(acc_g, sgs, cn.v[1] * 2, FX::q(gax, sg_g));
+                    acc_add<NL>(acc_g, sgs, cn.v[1] * 2 + 1, FX::q(gay, sg_g));
+                }
+                if (o2) {
+                    acc_add<NL>(acc_g, sgs, cn.v[2] * 2, FX::q(gbx, sg_g));
+                    acc_add<NL>(acc_g, sgs, cn.v[2] * 2 + 1, FX::q(gby, sg_g));
+                }
+                if (o0) {
+                    acc_add<NL>(acc_g, sgs, cn.v[0] * 2, FX::q(F::sgn(F::add(gax, gbx), -1.f), sg_g));
+                    acc_add<NL>(acc_g, sgs, cn.v[0] * 2 + 1, FX::q(F::sgn(F::add(gay, gby), -1.f), sg_g));
                 }
             }
         }
@@ -946,13 +1129,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                            F::half(F::det2(u[0], tt[1], u[1], tt[0]))};
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const long long qe = FX::q(nB[d], sg_e), qb = FX::q(nB[d], sg_b);
+                    const Lq qe = FX::q(nB[d], sg_e), qb = FX::q(nB[d], sg_b);
 #pragma unroll
                     for (int k = 0; k < 3; k++)
-                        if (f.e[k] < ti.n_eo) fx_add(acc_e + 2 * (f.e[k] * 3 + d), qe);
+                        if (f.e[k] < ti.n_eo) acc_add<NL>(acc_e, se, f.e[k] * 3 + d, qe);
 #pragma unroll
                     for (int k = 0; k < 3; k++)
-                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) fx_add(acc_b + 2 * (bmap[f.v[k]] * 3 + d), qb);
+                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) acc_add<NL>(acc_b, sb, bmap[f.v[k]] * 3 + d, qb);
                 }
             }
             if (WHAT & DO_ADJ) {
@@ -966,9 +1149,9 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                     V gq = F::mul(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]), f24);
                     V gr = F::mul(F::det2(WB[d1], u[d2], WB[d2], u[d1]), f24);
-                    if (f.v[1] < ti.n_own) fx_add(acc_g + 2 * (f.v[1] * 3 + d), FX::q(gq, sg_g));
-                    if (f.v[2] < ti.n_own) fx_add(acc_g + 2 * (f.v[2] * 3 + d), FX::q(gr, sg_g));
-                    if (f.v[0] < ti.n_own) fx_add(acc_g + 2 * (f.v[0] * 3 + d), FX::q(F::sgn(F::add(gq, gr), -1.f), sg_g));
+                    if (f.v[1] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[1] * 3 + d, FX::q(gq, sg_g));
+                    if (f.v[2] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[2] * 3 + d, FX::q(gr, sg_g));
+                    if (f.v[0] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[0] * 3 + d, FX::q(F::sgn(F::add(gq, gr), -1.f), sg_g));
                 }
             }
         } else {
@@ -976,11 +1159,11 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V nB[2] = {F::diff(xs[f.v[0] * 2 + 1], xs[f.v[1] * 2 + 1]), F::diff(xs[f.v[1] * 2 + 0], xs[f.v[0] * 2 + 0])};
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    if (f.e[0] < ti.n_eo) fx_add(acc_e + 2 * (f.e[0] * 2 + d), FX::q(F::half(nB[d]), sg_e));
-                    const long long qb = FX::q(nB[d], sg_b);
+                    if (f.e[0] < ti.n_eo) acc_add<NL>(acc_e, se, f.e[0] * 2 + d, FX::q(F::half(nB[d]), sg_e));
+                    const Lq qb = FX::q(nB[d], sg_b);
 #pragma unroll
                     for (int k = 0; k < 2; k++)
-                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) fx_add(acc_b + 2 * (bmap[f.v[k]] * 2 + d), qb);
+                        if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0) acc_add<NL>(acc_b, sb, bmap[f.v[k]] * 2 + d, qb);
                 }
             }
             if (WHAT & DO_ADJ) {
@@ -988,12 +1171,12 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V gx = F::mul(ws[f.e[0] * 2 + 1], f6);
                 V gy = F::sgn(F::mul(ws[f.e[0] * 2 + 0], f6), -1.f);
                 if (f.v[1] < ti.n_own) {
-                    fx_add(acc_g + 2 * (f.v[1] * 2), FX::q(gx, sg_g));
-                    fx_add(acc_g + 2 * (f.v[1] * 2 + 1), FX::q(gy, sg_g));
+                    acc_add<NL>(acc_g, sgs, f.v[1] * 2, FX::q(gx, sg_g));
+                    acc_add<NL>(acc_g, sgs, f.v[1] * 2 + 1, FX::q(gy, sg_g));
                 }
                 if (f.v[0] < ti.n_own) {
-                    fx_add(acc_g + 2 * (f.v[0] * 2), FX::q(F::sgn(gx, -1.f), sg_g));
-                    fx_add(acc_g + 2 * (f.v[0] * 2 + 1), FX::q(F::sgn(gy, -1.f), sg_g));
+                    acc_add<NL>(acc_g, sgs, f.v[0] * 2, FX::q(F::sgn(gx, -1.f), sg_g));
+                    acc_add<NL>(acc_g, sgs, f.v[0] * 2 + 1, FX::q(F::sgn(gy, -1.f), sg_g));
                 }
             }
         }
@@ -1005,14 +1188,14 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
     if (WHAT & DO_FWD) {
         for (int q = tid; q < ti.n_eo * DIM; q += NT)
-            A.n_out[int64_t(ti.edge0) * DIM + q] = FX::out(fx_load(acc_e + 2 * q), sg_e, esc);
+            A.n_out[int64_t(ti.edge0) * DIM + q] = FX::out(acc_load<NL>(acc_e, se, q), sg_e, esc);
         for (int q = tid; q < ti.n_bo * DIM; q += NT)
-            A.bnormal[int64_t(ti.bnode0) * DIM + q] = FX::out(fx_load(acc_b + 2 * q), sg_b, bsc);
-        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = FX::out(fx_load(acc_v + 2 * q), sg_v, vsc);
+            A.bnormal[int64_t(ti.bnode0) * DIM + q] = FX::out(acc_load<NL>(acc_b, sb, q), sg_b, bsc);
+        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = FX::out(acc_load<NL>(acc_v, sv, q), sg_v, vsc);
     }
     if (WHAT & DO_ADJ)
         for (int q = tid; q < ti.n_own * DIM; q += NT)
-            A.grad[int64_t(ti.node0) * DIM + q] = FX::out(fx_load(acc_g + 2 * q), sg_g, 1.0);
+            A.grad[int64_t(ti.node0) * DIM + q] = FX::out(acc_load<NL>(acc_g, sgs, q), sg_g, 1.0);
 }
 
 template <int DIM, int PREC, int WHAT>
@@ -1025,6 +1208,10 @@ template <int DIM, int PREC, int WHAT>
 int launch_tiles_scatter(const em_mesh* m, TileArgs& A, cudaStream_t s) {
     const SmemS L = smem_layout_s<DIM, PREC, WHAT>(A.D);
     static size_t configured = 0;
+    // a limb plane entry holds < 1024 contributions of magnitude <= 2^21
+    if (A.val_e > 1000 || A.val_v > 250)
+        return fail(EM_ERR_ARG, "tiled path: an edge with more than 1000 elements or a node with more than 250 "
+                                "elements exceeds its fixed-point headroom; use the gather path");
     if (L.total > 227 * 1024)
         return fail(EM_ERR_ARG, "tile needs " + std::to_string(L.total) +
                                     " bytes of shared memory (> 227 KB): rebuild the plan with a smaller tile_nodes");
