@@ -137,10 +137,14 @@ __global__ void k_count_bface(int dim, int64_t nbf, const int32_t* bface, int T,
 }
 
 // ---- pairs ------------------------------------------------------------------
-// key = tile << 4 | owned mask (bit r: the r-th smallest node of the element
-// belongs to the tile).  Sorting by it groups a tile's elements by which of
-// their nodes (and hence, by lower end, which of their edges) the tile owns,
-// so the threads of a warp mostly share one mask and skip the same outputs.
+// key = tile << 9 | owned mask << 5 | (element id mod 32) (mask bit r: the
+// r-th smallest node of the element belongs to the tile).  Sorting by it
+// groups a tile's elements by which of their nodes (and hence, by lower end,
+// which of their edges) the tile owns, so the threads of a warp mostly share
+// one mask and skip the same outputs; inside a group, elements whose ids
+// differ by a multiple of 32 come together, so the 32 elements a warp takes
+// lie far apart on the (spatially ordered) grid and rarely add into the same
+// node or edge in one atomic instruction.
 __global__ void k_fill_pairs(int dim, int64_t ne, const int32_t* elems, int T, const int64_t* off, uint64_t* keys,
                              uint32_t* vals) {
     GRID_LOOP(E, ne) {
@@ -152,13 +156,13 @@ __global__ void k_fill_pairs(int dim, int64_t ne, const int32_t* elems, int T, c
             unsigned mask = 0;
             for (int r = 0; r <= dim; r++)
                 if (v[r] / T == t[a]) mask |= 1u << r;
-            keys[o + a] = ((uint64_t)t[a] << 4) | mask;
+            keys[o + a] = ((uint64_t)t[a] << 9) | (mask << 5) | ((uint64_t)E & 31u);
             vals[o + a] = (uint32_t)E;
         }
     }
 }
 __global__ void k_key_drop_mask(int64_t n, uint64_t* keys) {
-    GRID_LOOP(i, n) keys[i] >>= 4;
+    GRID_LOOP(i, n) keys[i] >>= 9;
 }
 
 __global__ void k_fill_bpairs(int dim, int64_t nbf, const int32_t* bface, int T, const int64_t* off, uint64_t* keys,
@@ -558,7 +562,7 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     const int bt = bits_for(std::max<int64_t>(n_tiles - 1, 1));
     const int bn = bits_for(nv - 1);
     const int be = bits_for(n_edges - 1);
-    if (bt + bn > 63 || bt + be > 63 || bt + 4 > 63) return fail(EM_ERR_ARG, "grid too large for the tile keys");
+    if (bt + bn > 63 || bt + be > 63 || bt + 9 > 63) return fail(EM_ERR_ARG, "grid too large for the tile keys");
 
     if (*ws_bytes < full_bytes) {
         if (plan) return fail(EM_ERR_WORKSPACE, "plan workspace too small: need " + std::to_string(full_bytes));
@@ -571,7 +575,7 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
 
     // 1. pairs (tile, element), elements ascending inside a tile (stable sort)
     k_fill_pairs<<<G(ne), NT, 0, s>>>(dim, ne, elems, T, poff, pk, pv);
-    EM_TRY(radix_sort_pairs(pk, pv, kt, vt, P, bt + 4, sort_ws, s));
+    EM_TRY(radix_sort_pairs(pk, pv, kt, vt, P, bt + 9, sort_ws, s));
     k_key_drop_mask<<<G(P), NT, 0, s>>>(P, pk);
     EM_TRY(exclusive_scan_i32_to_i64(tile_cnt, el_off, n_tiles, scan_b, s));
 

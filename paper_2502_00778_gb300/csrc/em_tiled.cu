@@ -649,41 +649,6 @@ struct Fix<EM_PREC_FP64> {
     static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
 };
 
-// int64 * 2^-sg * sc -> double without FP64 instructions: the integer is cut
-// into a double-word (its top 24 bits and the next 24), scaled in double-word
-// arithmetic and rounded to double; 2^-sg is applied through the exponent
-__device__ __forceinline__ double fx_out_dw(long long q, int sg, double sc) {
-    if (q == 0) return 0.0;
-    const unsigned long long m = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
-    const int e = 63 - __clzll((long long)m);            // 2^e <= m < 2^(e+1)
-    const int sh = e - 23;
-    unsigned hb;
-    unsigned long long rest = 0;
-    if (sh > 0) {
-        hb = (unsigned)(m >> sh);
-        rest = m - ((unsigned long long)hb << sh);
-    } else {
-        hb = (unsigned)(m << (-sh));
-    }
-    float h = __uint_as_float(((unsigned)(e + 127) << 23) | (hb & 0x7fffffu));
-    float l = 0.f;
-    if (rest) {
-        const int sl = sh > 24 ? sh - 24 : 0;                 // keep the top 24 bits of rest
-        l = __fmul_rn(__uint2float_rn((unsigned)(rest >> sl)), pow2f(sl));
-    }
-    if (q < 0) {
-        h = -h;
-        l = -l;
-    }
-    const dw c = dw_from_double(sc);
-    const double d = dw_to_double(dw_mulc(dw{h, l}, c.h, c.l));
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const long long ex = (long long)((b >> 52) & 0x7ff) - sg;
-    if (ex <= 0) return 0.0;
-    b = (b & ~(0x7ffULL << 52)) | ((unsigned long long)ex << 52);
-    return __longlong_as_double((long long)b);
-}
-
 template <>
 struct Fix<EM_PREC_DW> {
     static constexpr int NL = 3, TOP = 62, LO = -60, HI = 120;
@@ -701,7 +666,8 @@ struct Fix<EM_PREC_DW> {
     static __device__ __forceinline__ unsigned mag(dw v) {
         return mkey(f_to_double((fabsf(v.h) + fabsf(v.l)) * 1.000001f));
     }
-    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return fx_out_dw(q, sg, sc); }
+    // once per output: the FP64 pipe is otherwise idle in this form
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
 };
 
 template <>
@@ -714,7 +680,7 @@ struct Fix<EM_PREC_MIXED> {
         return {a, b, 0};
     }
     static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
-    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return fx_out_dw(q, sg, sc); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
 };
 
 // key of an upper bound on |a - b| for two staged coordinates
@@ -747,7 +713,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
     s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
     s.bmap = take(sizeof(int) * D.max_own);
-    s.red = take(sizeof(unsigned) * 12);
+    s.red = take(sizeof(unsigned) * 16);
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -783,7 +749,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const int nnodes = ti.n_own + ti.n_halo;
 
     // ---- clear accumulators --------------------------------------------------
-    if (tid < 12) red[tid] = 0u;
+    if (tid < 16) red[tid] = 0u;
     if (WHAT & DO_FWD) {
         for (int q = tid; q < NL * se; q += NT) acc_e[q] = 0;
         for (int q = tid; q < NL * sv; q += NT) acc_v[q] = 0;
@@ -800,9 +766,9 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
     // gathers are issued in batches of SB per thread so that several loads are
     // in flight before the first one is used
-    constexpr int SB = 4;
+    constexpr int SB = 4, SBW = 8;
     unsigned wm = 0u, cm = 0u;
-    float xl = 0.f;   // largest |low part| of a staged coordinate (DW forms)
+    float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
     for (int i0 = tid; i0 < nnodes; i0 += SB * NT) {
         int64_t v[SB];
 #pragma unroll
@@ -837,21 +803,21 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     }
     if (WHAT & DO_ADJ) {
         const int nte = ti.n_eo + ti.n_hedge;
-        for (int i0 = tid; i0 < nte; i0 += SB * NT) {
-            int64_t e[SB];
+        for (int i0 = tid; i0 < nte; i0 += SBW * NT) {
+            int64_t e[SBW];
 #pragma unroll
-            for (int u = 0; u < SB; u++) {
+            for (int u = 0; u < SBW; u++) {
                 const int i = i0 + u * NT;
                 e[u] = i >= nte ? -1 : (i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]));
             }
-            double wv[SB][DIM];
+            double wv[SBW][DIM];
 #pragma unroll
-            for (int u = 0; u < SB; u++)
+            for (int u = 0; u < SBW; u++)
                 if (e[u] >= 0)
 #pragma unroll
                     for (int d = 0; d < DIM; d++) wv[u][d] = A.w[e[u] * DIM + d];
 #pragma unroll
-            for (int u = 0; u < SB; u++) {
+            for (int u = 0; u < SBW; u++) {
                 if (e[u] < 0) continue;
                 const int i = i0 + u * NT;
 #pragma unroll
@@ -875,33 +841,37 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     // from local node 0 of a tile element; every face vector, volume and
     // gradient term below is bounded by a power of Lx (edges not at node 0 and
     // boundary-face edges by 2 Lx), so the scales follow the element size, not
-    // the extent of the tile
-    if constexpr (PREC == EM_PREC_FP64) {
-        unsigned lm = 0u;
-        for (int i = tid; i < ti.n_el; i += NT) {
-            const ElemConn cn = conn[i];
+    // the extent of the tile.  The element records are loaded EB at a time so
+    // that their loads are in flight together.
+    {
+        constexpr int EB = 8;
+        unsigned lk = 0u;
+        float lf = 0.f;
+        for (int i0 = tid; i0 < ti.n_el; i0 += EB * NT) {
+            ElemConn cb[EB];
 #pragma unroll
-            for (int r = 1; r <= DIM; r++)
+            for (int u = 0; u < EB; u++)
+                if (i0 + u * NT < ti.n_el) cb[u] = conn[i0 + u * NT];
 #pragma unroll
-                for (int d = 0; d < DIM; d++) lm = max(lm, mkey(xs[cn.v[r] * DIM + d] - xs[cn.v[0] * DIM + d]));
+            for (int u = 0; u < EB; u++) {
+                if (i0 + u * NT >= ti.n_el) continue;
+#pragma unroll
+                for (int r = 1; r <= DIM; r++)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) {
+                        if constexpr (PREC == EM_PREC_FP64)
+                            lk = max(lk, mkey(xs[cb[u].v[r] * DIM + d] - xs[cb[u].v[0] * DIM + d]));
+                        else
+                            lf = fmaxf(lf, fabsf(__fsub_rn(xs[cb[u].v[r] * DIM + d].h, xs[cb[u].v[0] * DIM + d].h)));
+                    }
+            }
         }
-        block_max(red + 0, lm);
-    } else {
-        // high parts only: |a - b| <= |a.h - b.h| (1 + 2^-23) + 2 max|low part|
-        float lm = 0.f;
-        for (int i = tid; i < ti.n_el; i += NT) {
-            const ElemConn cn = conn[i];
-#pragma unroll
-            for (int r = 1; r <= DIM; r++)
-#pragma unroll
-                for (int d = 0; d < DIM; d++)
-                    lm = fmaxf(lm, fabsf(__fsub_rn(xs[cn.v[r] * DIM + d].h, xs[cn.v[0] * DIM + d].h)));
-        }
-        block_max(red + 0, mkey(f_to_double(lm)));
+        // DW / MIXED: |a - b| <= |a.h - b.h| (1 + 2^-23) + 2 max|low part|
+        block_max(red + 0, PREC == EM_PREC_FP64 ? lk : mkey(f_to_double(lf)));
     }
     __syncthreads();
 
-    // ---- scales: no accumulated sum can exceed bound * 2^sigma < 2^61 ---------
+    // ---- scales: no accumulated sum can reach 2^TOP -------------------------
     // one thread derives the scales (double arithmetic), the block reads them
     int* sgv = reinterpret_cast<int*>(red + 4);
     if (tid == 0) {
@@ -978,25 +948,29 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             const bool o0 = cn.v[0] < ti.n_own, o1 = cn.v[1] < ti.n_own, o2 = cn.v[2] < ti.n_own,
                        o3 = cn.v[3] < ti.n_own;
             if (WHAT & DO_FWD) {
-                // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2
+                // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2.
+                // An edge is owned exactly when its lower end is, and owned
+                // edges have local ids below n_eo (plan invariant).
+                if (o0) {
 #pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    if (o0) {
+                    for (int d = 0; d < 3; d++) {
                         const Lq q0 = FX::q(F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s), sg_e);
-#pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            if (ee.e[k] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[k] * 3 + d, q0);
+                        acc_add<NL>(acc_e, se, ee.e[0] * 3 + d, q0);
+                        acc_add<NL>(acc_e, se, ee.e[1] * 3 + d, q0);
+                        acc_add<NL>(acc_e, se, ee.e[2] * 3 + d, q0);
                     }
-                    if (o1) {
+                }
+                if (o1) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
                         const Lq q1 = FX::q(F::sgn(N1[d], -s), sg_e);
+                        acc_add<NL>(acc_e, se, ee.e[3] * 3 + d, q1);
+                        acc_add<NL>(acc_e, se, ee.e[4] * 3 + d, q1);
+                    }
+                }
+                if (o2) {
 #pragma unroll
-                        for (int k = 3; k < 5; k++)
-                            if (ee.e[k] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[k] * 3 + d, q1);
-                    }
-                    if (o2) {
-                        const Lq q2 = FX::q(F::sgn(N2[d], -s), sg_e);
-                        if (ee.e[5] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[5] * 3 + d, q2);
-                    }
+                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_e, se, ee.e[5] * 3 + d, FX::q(F::sgn(N2[d], -s), sg_e));
                 }
                 const Lq qv = FX::q(F::sgn(det, s), sg_v);
                 if (o0) acc_add<NL>(acc_v, sv, cn.v[0], qv);
@@ -1023,27 +997,57 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
                 V h = F::sgn(F::mul(Cs, f24), s);
                 // g_i is needed for owned node i, and all three for node 0
-                const bool na = o0 || o1, nb = o0 || o2, nc = o0 || o3;
+                V g1[3], g2[3], g3[3];
+                if (o0 || o1) {
 #pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                    V g1 = F::cst(0.0), g2 = F::cst(0.0), g3 = F::cst(0.0);
-                    if (na) {
+                    for (int d = 0; d < 3; d++) {
+                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                         V ga = F::sub(F::det2(A2[d1], c[d2], A2[d2], c[d1]), F::det2(A3[d1], b[d2], A3[d2], b[d1]));
-                        g1 = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
+                        g1[d] = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
                     }
-                    if (nb) {
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) g1[d] = F::cst(0.0);
+                }
+                if (o0 || o2) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                         V gb = F::sub(F::det2(A3[d1], a[d2], A3[d2], a[d1]), F::det2(A1[d1], c[d2], A1[d2], c[d1]));
-                        g2 = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
+                        g2[d] = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
                     }
-                    if (nc) {
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) g2[d] = F::cst(0.0);
+                }
+                if (o0 || o3) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                         V gc = F::sub(F::det2(A1[d1], b[d2], A1[d2], b[d1]), F::det2(A2[d1], a[d2], A2[d2], a[d1]));
-                        g3 = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
+                        g3[d] = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
                     }
-                    if (o1) acc_add<NL>(acc_g, sgs, cn.v[1] * 3 + d, FX::q(g1, sg_g));
-                    if (o2) acc_add<NL>(acc_g, sgs, cn.v[2] * 3 + d, FX::q(g2, sg_g));
-                    if (o3) acc_add<NL>(acc_g, sgs, cn.v[3] * 3 + d, FX::q(g3, sg_g));
-                    if (o0) acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d, FX::q(F::sgn(F::add(F::add(g1, g2), g3), -1.f), sg_g));
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) g3[d] = F::cst(0.0);
+                }
+                if (o1) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[1] * 3 + d, FX::q(g1[d], sg_g));
+                }
+                if (o2) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[2] * 3 + d, FX::q(g2[d], sg_g));
+                }
+                if (o3) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[3] * 3 + d, FX::q(g3[d], sg_g));
+                }
+                if (o0) {
+#pragma unroll
+                    for (int d = 0; d < 3; d++)
+                        acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d,
+                                    FX::q(F::sgn(F::add(F::add(g1[d], g2[d]), g3[d]), -1.f), sg_g));
                 }
             }
         } else {
@@ -1060,17 +1064,17 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             if (WHAT & DO_FWD) {
                 V n1[2] = {F::sgn(b[1], -s), F::sgn(b[0], s)};
                 V n2[2] = {F::sgn(a[1], s), F::sgn(a[0], -s)};
+                if (o0) {
 #pragma unroll
-                for (int d = 0; d < 2; d++) {
-                    if (o0) {
+                    for (int d = 0; d < 2; d++) {
                         const Lq q0 = FX::q(F::sgn(F::add(n1[d], n2[d]), -1.f), sg_e);
-                        if (ee.e[0] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[0] * 2 + d, q0);
-                        if (ee.e[1] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[1] * 2 + d, q0);
+                        acc_add<NL>(acc_e, se, ee.e[0] * 2 + d, q0);
+                        acc_add<NL>(acc_e, se, ee.e[1] * 2 + d, q0);
                     }
-                    if (o1) {
-                        const Lq q1 = FX::q(n1[d], sg_e);
-                        if (ee.e[2] < ti.n_eo) acc_add<NL>(acc_e, se, ee.e[2] * 2 + d, q1);
-                    }
+                }
+                if (o1) {
+#pragma unroll
+                    for (int d = 0; d < 2; d++) acc_add<NL>(acc_e, se, ee.e[2] * 2 + d, FX::q(n1[d], sg_e));
                 }
                 const Lq qv = FX::q(F::sgn(det, s), sg_v);
                 if (o0) acc_add<NL>(acc_v, sv, cn.v[0], qv);
@@ -1198,8 +1202,14 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             A.grad[int64_t(ti.node0) * DIM + q] = FX::out(acc_load<NL>(acc_g, sgs, q), sg_g, 1.0);
 }
 
+// resident CTAs per SM the register allocation must allow: the forward alone
+// and the FP32 form need little shared memory and fit three CTAs, the other
+// adjoint-carrying forms fit two
+template <int PREC, int WHAT>
+constexpr int scatter_min_ctas() { return (PREC == EM_PREC_MIXED || WHAT == DO_FWD) ? 3 : 2; }
+
 template <int DIM, int PREC, int WHAT>
-__global__ void __launch_bounds__(NT) k_tile_scatter(TileArgs A) {
+__global__ void __launch_bounds__(NT, scatter_min_ctas<PREC, WHAT>()) k_tile_scatter(TileArgs A) {
     extern __shared__ __align__(16) char smem[];
     run_tile_scatter<DIM, PREC, WHAT>(A, (int)(A.tile_base + blockIdx.x), smem);
 }
