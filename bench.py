@@ -387,8 +387,17 @@ def run_ours(args):
         if have_gather:
             cand += [("fwd:tiled", q_) for q_ in ("fp64", "dw", "mixed")]
         fwd_bytes = algorithmic_bytes(m, topo, "fwd", path)
+        fwd_tile = None
         for pth, pr in cand:
             try:
+                if pth == "fwd:tiled" and fwd_tile is None:
+                    # the forward alone needs less shared memory per tile:
+                    # tune its tile size separately
+                    from paper_2502_00778_gb300 import autotune
+                    _, fwd_tile, fsweep = autotune.tune(topo, x, what="fwd", precision="dw",
+                                                        candidates=(96, 128, 192, 256), paths=("tiled",),
+                                                        use_cache=False)
+                    forms["fwd:tiled tile_nodes"] = {"tile_nodes": fwd_tile, "sweep_ms": fsweep}
                 def fstep():
                     if pth.startswith("fwd:"):
                         api.edge_metrics(topo, x, pr, pth[4:], out=outs[:3])

@@ -271,6 +271,10 @@ WORKLOADS = {
     "kuhn160_off1e3": (kuhn_cube, dict(n=160, jitter=0.2, seed=SEED_BASE + 3, permute=True, morton=True,
                                        offset=1000.0)),
     "kuhn96": (kuhn_cube, dict(n=96, jitter=0.2, seed=SEED_BASE + 4, permute=True, morton=True)),
+    # the paper's largest 3D grid size (Sec. 5: 16,974,593 nodes, 100,663,296 tets)
+    "kuhn256": (kuhn_cube, dict(n=256, jitter=0.2, seed=SEED_BASE + 8, permute=True, morton=True)),
+    # the paper's 2D grid size (65,536 nodes, 130,050 triangles)
+    "tri255": (tri_square, dict(n=255, jitter=0.2, seed=SEED_BASE + 9, permute=True, morton=True)),
 }
 
 

@@ -1,7 +1,9 @@
 """Full-size checks in the benchmark's configuration.
 
-160^3 x 6 tets, offset 1e3 (the benchmark workload), tile size chosen as in
-the benchmark: edge_build is checked through properties that characterise
+160^3 x 6 tets, offset 1e3 (the benchmark workload), in the benchmark's
+launch configuration (fused tiled scatter, tile_nodes 96 as the autotuner
+picks it for the fused double-word step, one launch per step; the ordered
+gather path for comparison): edge_build is checked through properties that characterise
 the sorted unique edge list exactly; the metrics and the adjoint are checked
 at 2000 sampled edges and nodes, each computed by the oracle alone from the
 elements around it.  96^3 x 6 (the adjoint workload): the full gradient
@@ -35,7 +37,7 @@ def big():
     x = torch.from_numpy(m.x).to(DEV)
     el = torch.from_numpy(m.elems).to(DEV)
     topo = api.edge_build(el, x)
-    api.plan_build(topo, 128)
+    api.plan_build(topo, 96)
     return m, x, topo
 
 
@@ -60,8 +62,8 @@ def test_edge_build_properties_160(big):
     assert topo.n_bnodes == (n + 1) ** 3 - (n - 1) ** 3
 
 
-@pytest.mark.parametrize("prec", ["dw", "fp64"])
-def test_sampled_parity_160(big, prec):
+@pytest.mark.parametrize("prec,path", [("dw", "tiled"), ("fp64", "tiled"), ("mixed", "tiled"), ("dw", "gather")])
+def test_sampled_parity_160(big, prec, path):
     from paper_2502_00778_gb300 import api
     m, x, topo = big
     e = topo.edges.cpu().numpy()
@@ -71,16 +73,20 @@ def test_sampled_parity_160(big, prec):
     ns = np.unique(np.concatenate([rng.choice(m.n_nodes, 1500, replace=False), rng.choice(bn, 500, replace=False)]))
     w, c = meshgen.generate.hash_weights(e, m.n_nodes, 3, SEED)
     wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
-    n, v, b, g = api.edge_metrics_fused(topo, x, wt, ct, prec)
+    n, v, b, g = api.edge_metrics_fused(topo, x, wt, ct, prec, path=path)
     rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], ns, SEED)
     h = m.h
-    assert np.abs(n.cpu().numpy()[es] - rn).max() <= 1e-12 * h * h
-    assert np.abs(v.cpu().numpy()[ns] - rv).max() <= 1e-12 * h ** 3
+    # FP64 contract; the FP32 element-math form at its stated accuracy
+    tn, tv, tg = (1e-12, 1e-12, 1e-12) if prec != "mixed" else (2e-6, 2e-6, 1e-5)
+    assert np.abs(n.cpu().numpy()[es] - rn).max() <= tn * h * h
+    assert np.abs(v.cpu().numpy()[ns] - rv).max() <= tv * h ** 3
     bfull = np.zeros((m.n_nodes, 3))
     bfull[bn] = b.cpu().numpy()
-    assert np.abs(bfull[ns] - rb).max() <= 1e-12 * h * h
+    assert np.abs(bfull[ns] - rb).max() <= tn * h * h
     gg = g.cpu().numpy()
-    assert np.abs(gg[ns] - rg).max() <= 1e-12 * np.abs(gg).max()
+    assert np.abs(gg[ns] - rg).max() <= tg * np.abs(gg).max()
+    if prec == "mixed":
+        return
     # properties at every node: closure and the volume sum
     a = np.zeros((m.n_nodes, 3))
     nn = n.cpu().numpy()
@@ -117,7 +123,7 @@ def test_adjoint_96_fd():
     wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
     rg = oracle.adjoint(3, m.x, m.elems, t, w, c)
     tol = 1e-12 * np.abs(rg).max()
-    for prec, path in [("dw", "gather"), ("fp64", "gather"), ("fp64", "atomic")]:
+    for prec, path in [("dw", "tiled"), ("fp64", "tiled"), ("dw", "gather"), ("fp64", "gather"), ("fp64", "atomic")]:
         g = api.edge_metrics_adjoint(topo, x, wt, ct, prec, path).cpu().numpy()
         assert np.abs(g - rg).max() <= tol, (prec, path)
     nodes = meshgen.generate.fd_nodes(m.n_nodes, 1000, seed=SEED + 6)
