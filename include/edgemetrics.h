@@ -323,7 +323,7 @@ int em_edge_metrics_noalloc(const em_mesh* mesh, const double* x,
 /* Batched meshes                                                            */
 /* ------------------------------------------------------------------------ */
 
-/* One mesh of a batch: everything em_edge_metrics_fused needs (GATHER plan
+/* One mesh of a batch: everything em_edge_metrics_fused needs (tile plan
  * required, mesh.plan_info filled) plus its inputs and outputs. */
 typedef struct em_batch_item {
     em_mesh mesh;
@@ -334,9 +334,11 @@ typedef struct em_batch_item {
 /* em_batched_fwd_adj -- forward + adjoint (as em_edge_metrics_fused) for
  * n_meshes grids of uneven size in ONE persistent launch.  The tiles of all
  * grids form one work list; resident blocks claim tiles through an atomic
- * counter and run each tile exactly as the single-grid gather path does, so
- * every output equals em_edge_metrics_fused's bit for bit.  No block waits
- * on another block.
+ * counter and run each tile exactly as the single-grid EM_PATH_TILED pass
+ * does (exact fixed-point accumulation), so every output equals
+ * em_edge_metrics_fused(..., EM_PATH_TILED) bit for bit.  No block waits on
+ * another block.  Grids with an edge valence above 1000 or a node valence
+ * above 250 are refused (EM_ERR_ARG), as in the tiled path.
  *   items        DEVICE array [n_meshes] of em_batch_item (pointers inside
  *                are device pointers); all grids must have the same dim.
  *   tile_prefix  DEVICE int64 [n_meshes+1]: exclusive prefix sum of the grids'

@@ -316,6 +316,31 @@ def cached_workload(name: str, cache_dir: str = None, **override) -> Mesh:
     return m
 
 
+def cached_batched_set(n_meshes: int = 64, cache_dir: str = None, **kw) -> list:
+    """batched_set(...) with an .npz cache (one file for the whole batch)."""
+    import hashlib
+    import json
+    import os
+    cache_dir = cache_dir or os.environ.get("EM_MESH_CACHE")
+    if not cache_dir:
+        return batched_set(n_meshes, **kw)
+    tag = hashlib.sha1(json.dumps(["batched", n_meshes, sorted(kw.items())], default=str).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir, f"batched{n_meshes}-{tag}.npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return [Mesh(name=f"batched{k}", dim=3, x=z[f"x{k}"], elems=z[f"e{k}"], h=float(z[f"h{k}"]), meta={})
+                for k in range(n_meshes)]
+    ms = batched_set(n_meshes, **kw)
+    os.makedirs(cache_dir, exist_ok=True)
+    arrs = {}
+    for k, m in enumerate(ms):
+        arrs[f"x{k}"], arrs[f"e{k}"], arrs[f"h{k}"] = m.x, m.elems, m.h
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, **arrs)
+    os.replace(tmp, path)
+    return ms
+
+
 # ----------------------------------------------------------------------------
 # counter-based loss weights: w(j,k) and c(v) as functions of node ids
 # (SplitMix64, Steele, Lea & Flood, OOPSLA 2014), so that a checker can

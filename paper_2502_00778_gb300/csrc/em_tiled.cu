@@ -43,23 +43,25 @@ struct Form;
 
 template <>
 struct Form<EM_PREC_FP64> {
+    // explicitly rounded operations: every kernel that inlines this form
+    // evaluates the same expressions (no compiler-chosen FMA contraction)
     using C = double;  // staged coordinate (raw)
     using V = double;  // element value
     using A = double;  // accumulator
     static __device__ __forceinline__ C coord(double x, double) { return x; }
-    static __device__ __forceinline__ V diff(C a, C b) { return a - b; }
-    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
-    static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
-    static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
-    static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return p * q - r * s; }
+    static __device__ __forceinline__ V diff(C a, C b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return __fma_rn(p, q, -__dmul_rn(r, s)); }
     static __device__ __forceinline__ V sgn(V a, float s) { return s < 0.f ? -a : a; }
-    static __device__ __forceinline__ V half(V a) { return 0.5 * a; }
+    static __device__ __forceinline__ V half(V a) { return __dmul_rn(0.5, a); }
     static __device__ __forceinline__ float sign_of(V a) { return a > 0.0 ? 1.f : -1.f; }
     static __device__ __forceinline__ V from_double(double d) { return d; }
     static __device__ __forceinline__ V cst(double d) { return d; }
     static __device__ __forceinline__ A zero() { return 0.0; }
-    static __device__ __forceinline__ void acc(A& a, V v) { a += v; }
-    static __device__ __forceinline__ double out(A a, double sc) { return a * sc; }
+    static __device__ __forceinline__ void acc(A& a, V v) { a = __dadd_rn(a, v); }
+    static __device__ __forceinline__ double out(A a, double sc) { return __dmul_rn(a, sc); }
 };
 
 template <>
@@ -642,11 +644,13 @@ template <>
 struct Fix<EM_PREC_FP64> {
     static constexpr int NL = 3, TOP = 62, LO = -900, HI = 900;
     static __device__ __forceinline__ Lq q(double v, int sg) {
-        const long long z = __double2ll_rn(v * pow2d(sg));    // FP64 pipe: this form is FP64-bound anyway
+        const long long z = __double2ll_rn(__dmul_rn(v, pow2d(sg)));   // FP64 pipe: this form is FP64-bound anyway
         return {(int)(z >> 42), (int)((z >> 21) & 0x1fffff), (int)(z & 0x1fffff)};
     }
     static __device__ __forceinline__ unsigned mag(double v) { return mkey(v); }
-    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) {
+        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+    }
 };
 
 template <>
@@ -667,7 +671,9 @@ struct Fix<EM_PREC_DW> {
         return mkey(f_to_double((fabsf(v.h) + fabsf(v.l)) * 1.000001f));
     }
     // once per output: the FP64 pipe is otherwise idle in this form
-    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) {
+        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+    }
 };
 
 template <>
@@ -680,7 +686,9 @@ struct Fix<EM_PREC_MIXED> {
         return {a, b, 0};
     }
     static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
-    static __device__ __forceinline__ double out(long long q, int sg, double sc) { return (double)q * (pow2d(-sg) * sc); }
+    static __device__ __forceinline__ double out(long long q, int sg, double sc) {
+        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+    }
 };
 
 // key of an upper bound on |a - b| for two staged coordinates
@@ -1286,6 +1294,9 @@ int dispatch_what(const em_mesh* m, int what, TileArgs& A, cudaStream_t s) {
 }
 
 // ---- batched: persistent blocks drain the tiles of many grids ---------------
+// Work item = (grid, tile), numbered through the grids' tile prefix sums; each
+// block claims items from one atomic counter and runs the tiled scatter on
+// them, so the results are those of the single-grid tiled path.
 __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs& A) {
     A.plan = it.mesh.plan;
     A.bnode = it.mesh.bnode;
@@ -1298,31 +1309,39 @@ __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs
 }
 
 template <int DIM, int PREC>
-__global__ void __launch_bounds__(NT) k_batched(const em_batch_item* __restrict__ items, const int64_t* __restrict__ prefix,
-                                               int n_meshes, Dims D, unsigned long long* counter, int32_t* status) {
+__global__ void __launch_bounds__(NT, (scatter_min_ctas<PREC, DO_FWD | DO_ADJ>()))
+    k_batched(const em_batch_item* __restrict__ items, const int64_t* __restrict__ prefix, int n_meshes, Dims D,
+              unsigned long long* counter, int32_t* status) {
     extern __shared__ __align__(16) char smem[];
     __shared__ long long s_next;
-    const int64_t total = prefix[n_meshes];
+    // the tile prefix sums live in shared memory behind the tile's layout
+    const SmemS L = smem_layout_s<DIM, PREC, DO_FWD | DO_ADJ>(D);
+    int64_t* spre = reinterpret_cast<int64_t*>(smem + L.total);
+    for (int i = threadIdx.x; i <= n_meshes; i += blockDim.x) spre[i] = prefix[i];
+    if (threadIdx.x == 0) s_next = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t total = spre[n_meshes];
     for (;;) {
-        if (threadIdx.x == 0) s_next = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
         const int64_t wk = s_next;
         __syncthreads();
         if (wk >= total) break;
+        // claim the following item now; its atomic completes while this tile runs
+        if (threadIdx.x == 0) s_next = (long long)atomicAdd(counter, 1ull);
         int lo = 0, hi = n_meshes - 1;           // last mesh whose prefix <= wk
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= wk) lo = mid; else hi = mid - 1;
+            if (spre[mid] <= wk) lo = mid; else hi = mid - 1;
         }
         const em_batch_item& it = items[lo];
-        if (it.mesh.dim != DIM) {
+        if (it.mesh.dim != DIM) {   // block-uniform branch
             if (threadIdx.x == 0) atomicExch(status, EM_ERR_ARG);
+            __syncthreads();         // orders the claim above before the next read of s_next
             continue;
         }
         TileArgs A;
         args_from_mesh(it, A);
         A.D = D;
-        run_tile<DIM, PREC, DO_FWD | DO_ADJ>(A, (int)(wk - prefix[lo]), smem);
+        run_tile_scatter<DIM, PREC, DO_FWD | DO_ADJ>(A, (int)(wk - prefix[lo]), smem);
         __syncthreads();
     }
 }
@@ -1330,17 +1349,18 @@ __global__ void __launch_bounds__(NT) k_batched(const em_batch_item* __restrict_
 template <int DIM, int PREC>
 int launch_batched(int n_meshes, const em_batch_item* items, const int64_t* prefix, const Dims& D, int blocks,
                    unsigned long long* counter, int32_t* status, cudaStream_t s) {
-    const Smem L = smem_layout<DIM, PREC, DO_FWD | DO_ADJ>(D);
-    if (L.total > 227 * 1024)
-        return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(L.total) +
-                                    " bytes of shared memory (> 227 KB): use a smaller tile_nodes");
-    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const SmemS L = smem_layout_s<DIM, PREC, DO_FWD | DO_ADJ>(D);
+    const size_t bytes = L.total + sizeof(int64_t) * (size_t)(n_meshes + 1);
+    if (bytes > 227 * 1024)
+        return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(bytes) +
+                                    " bytes of shared memory (> 227 KB): use a smaller tile_nodes or fewer grids");
+    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     if (blocks <= 0) {
         int per_sm = 0;
-        EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<DIM, PREC>, NT, L.total));
+        EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<DIM, PREC>, NT, bytes));
         blocks = num_sms() * (per_sm > 0 ? per_sm : 1);
     }
-    k_batched<DIM, PREC><<<blocks, NT, L.total, s>>>(items, prefix, n_meshes, D, counter, status);
+    k_batched<DIM, PREC><<<blocks, NT, bytes, s>>>(items, prefix, n_meshes, D, counter, status);
     note_launches(1);
     EM_CUDA_TRY(cudaGetLastError());
     return EM_OK;
@@ -1368,6 +1388,10 @@ int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_p
     D.max_ns = (int)max_info[EM_PLAN_INFO_MAX_NSLOTS];
     D.max_bs = (int)max_info[EM_PLAN_INFO_MAX_BSLOTS];
     if (D.max_own <= 0 || D.max_nodes <= 0) return fail(EM_ERR_ARG, "max_info is empty");
+    // each grid's tiles accumulate in exact fixed point (tiled scatter)
+    if (max_info[EM_PLAN_INFO_MAX_EDGE_VALENCE] > 1000 || max_info[EM_PLAN_INFO_MAX_NODE_VALENCE] > 250)
+        return fail(EM_ERR_ARG, "batched pass: an edge with more than 1000 elements or a node with more than 250 "
+                                "elements exceeds the fixed-point headroom");
     unsigned long long* counter = static_cast<unsigned long long*>(ws);
     EM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     EM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));

@@ -1,6 +1,6 @@
 """Batched forward + adjoint of uneven grids in one persistent launch, and
-its CUDA-graph replay: every output equals the per-grid fused pass bit for
-bit (same tiles, same code, fixed summation order)."""
+its CUDA-graph replay: every output equals the per-grid fused tiled pass
+bit for bit (same tiles, same code, exact fixed-point sums)."""
 import numpy as np
 import pytest
 
@@ -42,7 +42,7 @@ def test_batched_equals_per_grid(batch_inputs, prec):
     torch.cuda.synchronize()
     b.check_status()
     for t, x, w, c, o in zip(topos, xs, ws, cs, b.outs):
-        ref = api.edge_metrics_fused(t, x, w, c, prec)
+        ref = api.edge_metrics_fused(t, x, w, c, prec, path="tiled")
         for a, r in zip(o, ref):
             assert torch.equal(a, r)
 
