@@ -273,6 +273,20 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path,
 int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, double* vol,
                    void* ws, size_t* ws_bytes, void* stream);
 
+/* em_edge_residual -- the edge-loop residual of the edge-based
+ * discretization (Sec. 2) for a given nodal flux F [n_nodes][dim]:
+ *   res_j = sum_{edges {j,k}} phi_jk - sum_{edges {i,j}} phi_ij + F_j . bnormal_j,
+ *   phi_jk = sum_c 1/2 (F_j[c] + F_k[c]) n_jk[c]   (central flux),
+ * the boundary term only at boundary nodes (bnormal [n_bnodes][dim] in
+ * mesh->bnode order, as em_edge_metrics writes it).  For a linear F it equals
+ * V_j div F at every interior node.  One thread per node sums its edges in
+ * ascending edge id with explicitly rounded FP64 arithmetic (the same
+ * expression as a serial edge loop).  res [n_nodes] is overwritten.  Needs
+ * mesh->edges and mesh->bnode; lists are built in the workspace (size query
+ * with ws == NULL). */
+int em_edge_residual(const em_mesh* mesh, const double* F, const double* n_edge, const double* bnormal,
+                     double* res, void* ws, size_t* ws_bytes, void* stream);
+
 /* em_check_elements -- validation: counts elements with a node id outside
  * [0,n_nodes), a repeated node, or zero measure (det == 0 in FP64).
  *   ws       device workspace (size query with ws == NULL, as everywhere).

@@ -47,6 +47,8 @@ def lib():
             L.or_traditional.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i32p, _i64, _f64p]
             L.or_edge_volume.restype = None
             L.or_edge_volume.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _f64p, _f64p]
+            L.or_edge_residual.restype = None
+            L.or_edge_residual.argtypes = [ctypes.c_int, _i64, _i64, _i32p, _f64p, _f64p, _i64, _i32p, _f64p, _f64p]
             L.or_closure.restype = None
             L.or_closure.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _f64p, _i64, _i32p, _f64p]
             L.or_adjoint.restype = None
@@ -161,6 +163,19 @@ def edge_volume(dim, x, topo, n_edge):
     lib().or_edge_volume(dim, x.shape[0], _p(x, _f64p), topo.n_edges, _p(topo.edges, _i32p), _p(n_edge, _f64p),
                          _p(v, _f64p))
     return v
+
+
+def edge_residual(dim, topo, n_edge, F, bnormal):
+    """Edge-loop residual with central fluxes (Sec. 2) and the boundary term
+    F_j . bnormal_j; `bnormal` is [n_bnodes][dim] in topo.bnode order."""
+    n_edge = _c(n_edge, np.float64)
+    F = _c(F, np.float64)
+    bnormal = _c(bnormal, np.float64)
+    bn = _c(topo.bnode, np.int32)
+    res = np.empty(F.shape[0])
+    lib().or_edge_residual(dim, F.shape[0], topo.n_edges, _p(topo.edges, _i32p), _p(n_edge, _f64p), _p(F, _f64p),
+                           bn.shape[0], _p(bn, _i32p), _p(bnormal, _f64p), _p(res, _f64p))
+    return res
 
 
 def closure(dim, x, topo, n_edge):

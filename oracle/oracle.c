@@ -24,6 +24,9 @@
  *   or_traditional      dual-face construction (Sec. 3.1.1 / 3.1.2)
  *   or_edge_volume      edge-based dual volume (Sec. 4.1)
  *   or_closure          sum of directed areas per node (Sec. 3.2.3)
+ *   or_edge_residual    edge-loop residual of the edge-based discretization
+ *                       (Sec. 2): central flux 1/2 (F_j + F_k).n_jk out of
+ *                       j and into k, plus F_j.bnormal_j at boundary nodes
  *   or_adjoint          analytic gradient of L = sum_e w_e.n_e + sum_i c_i V_i
  *   or_loss_subset      L restricted to chosen elements / boundary faces
  *   or_fd_gradient      patch-local central differences of L
@@ -383,6 +386,30 @@ void or_edge_volume(int dim, int64_t nv, const double* x, int64_t nedges, const 
         vol[k] += s;
     }
     for (int64_t v = 0; v < nv; v++) vol[v] *= 1.0 / (2.0 * dim);
+}
+
+/* Edge-loop residual (Sec. 2): every edge {j,k} carries the central flux
+ * phi = sum_c 1/2 (F_j[c] + F_k[c]) n_jk[c] out of node j's dual volume and
+ * into node k's; a boundary node adds F_j . bnormal_j.  For a linear F the
+ * sum equals V_j div F at interior nodes (closure plus the linear exactness
+ * of the lumped areas); boundary nodes need a boundary quadrature that this
+ * simple closure does not provide. */
+void or_edge_residual(int dim, int64_t nv, int64_t nedges, const int32_t* edges, const double* n_edge, const double* F,
+                      int64_t nbn, const int32_t* bnode, const double* bnormal, double* res) {
+    memset(res, 0, sizeof(double) * (size_t)nv);
+    for (int64_t e = 0; e < nedges; e++) {
+        int32_t j = edges[2 * e], k = edges[2 * e + 1];
+        double phi = 0;
+        for (int c = 0; c < dim; c++) phi += 0.5 * (F[dim * j + c] + F[dim * k + c]) * n_edge[dim * e + c];
+        res[j] += phi;
+        res[k] -= phi;
+    }
+    for (int64_t b = 0; b < nbn; b++) {
+        int32_t j = bnode[b];
+        double s = 0;
+        for (int c = 0; c < dim; c++) s += F[dim * j + c] * bnormal[dim * b + c];
+        res[j] += s;
+    }
 }
 
 void or_closure(int dim, int64_t nv, const double* x, int64_t nedges, const int32_t* edges, const double* n_edge,

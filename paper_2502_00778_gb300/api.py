@@ -259,6 +259,24 @@ def edge_volume(topo: Topology, x, n_edge):
     return v
 
 
+def edge_residual(topo: Topology, F, n_edge, bnormal):
+    """Edge-loop residual with central fluxes (Sec. 2) for nodal fluxes F."""
+    L = load()
+    _require_cuda(F, n_edge, bnormal)
+    F = F.contiguous().to(torch.float64)
+    n_edge = n_edge.contiguous().to(torch.float64)
+    bnormal = bnormal.contiguous().to(torch.float64)
+    res = torch.empty(topo.n_nodes, dtype=torch.float64, device=F.device)
+    m, mr = _mesh_ref(topo)
+    wsb = ctypes.c_size_t(0)
+    null = ctypes.c_void_p(0)
+    check(L.em_edge_residual(mr, _ptr(F), _ptr(n_edge), _ptr(bnormal), _ptr(res), null, ctypes.byref(wsb), _stream()))
+    ws = workspace.get(wsb.value, F.device)
+    check(L.em_edge_residual(mr, _ptr(F), _ptr(n_edge), _ptr(bnormal), _ptr(res), _ptr(ws), ctypes.byref(wsb),
+                             _stream()))
+    return res
+
+
 def check_elements(dim: int, elems: torch.Tensor, x: torch.Tensor):
     """(bad-id count, degenerate count); raises EMError on either."""
     L = load()

@@ -183,6 +183,21 @@ int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, d
     return st == EM_OK ? ok() : st;
 }
 
+int em_edge_residual(const em_mesh* mesh, const double* F, const double* n_edge, const double* bnormal, double* res,
+                     void* ws, size_t* ws_bytes, void* stream) {
+    if (!mesh) return fail(EM_ERR_ARG, "mesh is NULL");
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(EM_ERR_ARG, "mesh->dim must be 2 or 3");
+    if (mesh->n_nodes <= 0 || mesh->n_edges <= 0 || !mesh->edges) return fail(EM_ERR_ARG, "mesh needs edges");
+    if (mesh->n_bnodes < 0 || (mesh->n_bnodes && !mesh->bnode)) return fail(EM_ERR_ARG, "mesh needs bnode");
+    bool query;
+    EM_TRY(check_ws(ws, ws_bytes, edge_volume_ws_bytes(mesh), &query));
+    if (query) return ok();
+    if (!F || !n_edge || !res || (mesh->n_bnodes && !bnormal))
+        return fail(EM_ERR_ARG, "F, n_edge, bnormal and res must not be NULL");
+    int st = edge_residual(mesh, F, n_edge, bnormal, res, ws, as_stream(stream));
+    return st == EM_OK ? ok() : st;
+}
+
 int em_edge_metrics_noalloc(const em_mesh* mesh, const double* x, double* n_edge, double* vol, double* bnormal,
                             void* stream) {
     EM_TRY(check_mesh(mesh));

@@ -265,6 +265,36 @@ __global__ void k_edge_volume(int64_t nv, const int64_t* __restrict__ off, const
     }
 }
 
+// edge-loop residual (Sec. 2): central flux out of the lower end, into the
+// upper end, plus F . bnormal at boundary nodes; per node in ascending edge id
+__global__ void k_bnode_map(int64_t nbn, const int32_t* __restrict__ bnode, int32_t* __restrict__ bmap) {
+    GLOOP(b, nbn) bmap[bnode[b]] = (int32_t)b;
+}
+template <int DIM>
+__global__ void k_edge_residual(int64_t nv, const int64_t* __restrict__ off, const int32_t* __restrict__ ent,
+                                const int32_t* __restrict__ edges, const double* __restrict__ F,
+                                const double* __restrict__ n, const int32_t* __restrict__ bmap,
+                                const double* __restrict__ bnormal, double* __restrict__ res) {
+    GLOOP(i, nv) {
+        double acc = 0.0;
+        for (int64_t q = off[i]; q < off[i + 1]; q++) {
+            const int64_t e = ent[q];
+            const int64_t j = edges[2 * e], k = edges[2 * e + 1];
+            double phi = 0.0;
+            for (int c = 0; c < DIM; c++)
+                phi = P(phi, M(M(0.5, P(F[DIM * j + c], F[DIM * k + c])), n[DIM * e + c]));
+            acc = (j == i) ? P(acc, phi) : S(acc, phi);
+        }
+        const int32_t b = bmap[i];
+        if (b >= 0) {
+            double t = 0.0;
+            for (int c = 0; c < DIM; c++) t = P(t, M(F[DIM * i + c], bnormal[DIM * int64_t(b) + c]));
+            acc = P(acc, t);
+        }
+        res[i] = acc;
+    }
+}
+
 #undef GLOOP
 
 inline unsigned Gc(int64_t n) { return grid_for(n, NTC); }
@@ -298,7 +328,7 @@ CsrWs csr_layout(const em_mesh* m, void* ws, size_t* bytes) {
 }
 
 struct EvWs {
-    int32_t *cnt, *fill, *ent;
+    int32_t *cnt, *fill, *ent, *bmap;
     int64_t* off;
     void* scan;
 };
@@ -309,9 +339,23 @@ EvWs ev_layout(const em_mesh* m, void* ws, size_t* bytes) {
     w.fill = L.take<int32_t>(m->n_nodes + 1);
     w.off = L.take<int64_t>(m->n_nodes + 1);
     w.ent = L.take<int32_t>(2 * m->n_edges);
+    w.bmap = L.take<int32_t>(m->n_nodes);
     w.scan = L.take<char>(scan_ws_bytes(m->n_nodes + 1));
     if (bytes) *bytes = L.bytes();
     return w;
+}
+
+// node -> incident edges, each list ascending (shared by the edge-based
+// volume and the edge-loop residual)
+int node_edge_lists(const em_mesh* m, const EvWs& w, cudaStream_t s) {
+    EM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * (m->n_nodes + 1), s));
+    EM_CUDA_TRY(cudaMemsetAsync(w.fill, 0, 4 * (m->n_nodes + 1), s));
+    k_edge_node_count<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.cnt);
+    EM_TRY(exclusive_scan_i32_to_i64(w.cnt, w.off, m->n_nodes, w.scan, s));
+    k_edge_node_fill<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.off, w.fill, w.ent);
+    k_sort_lists<<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent);
+    note_launches(3 + 3);
+    return EM_OK;
 }
 
 }  // namespace
@@ -324,15 +368,25 @@ size_t edge_volume_ws_bytes(const em_mesh* m) {
 
 int edge_volume(const em_mesh* m, const double* x, const double* n, double* vol, void* ws, cudaStream_t s) {
     EvWs w = ev_layout(m, ws, nullptr);
-    EM_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, 4 * (m->n_nodes + 1), s));
-    EM_CUDA_TRY(cudaMemsetAsync(w.fill, 0, 4 * (m->n_nodes + 1), s));
-    k_edge_node_count<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.cnt);
-    EM_TRY(exclusive_scan_i32_to_i64(w.cnt, w.off, m->n_nodes, w.scan, s));
-    k_edge_node_fill<<<Gc(m->n_edges), NTC, 0, s>>>(m->n_edges, m->edges, w.off, w.fill, w.ent);
-    k_sort_lists<<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent);
+    EM_TRY(node_edge_lists(m, w, s));
     if (m->dim == 3) k_edge_volume<3><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, x, n, vol);
     else k_edge_volume<2><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, x, n, vol);
-    note_launches(4 + 3);
+    note_launches(1);
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+int edge_residual(const em_mesh* m, const double* F, const double* n, const double* bnormal, double* res, void* ws,
+                  cudaStream_t s) {
+    EvWs w = ev_layout(m, ws, nullptr);
+    EM_TRY(node_edge_lists(m, w, s));
+    EM_CUDA_TRY(cudaMemsetAsync(w.bmap, 0xff, 4 * m->n_nodes, s));
+    if (m->n_bnodes) k_bnode_map<<<Gc(m->n_bnodes), NTC, 0, s>>>(m->n_bnodes, m->bnode, w.bmap);
+    if (m->dim == 3)
+        k_edge_residual<3><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, F, n, w.bmap, bnormal, res);
+    else
+        k_edge_residual<2><<<Gc(m->n_nodes), NTC, 0, s>>>(m->n_nodes, w.off, w.ent, m->edges, F, n, w.bmap, bnormal, res);
+    note_launches(m->n_bnodes ? 2 : 1);
     EM_CUDA_TRY(cudaGetLastError());
     return EM_OK;
 }

@@ -32,6 +32,8 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
 size_t csr_fwd_ws_bytes(const em_mesh* m);
 size_t edge_volume_ws_bytes(const em_mesh* m);
 int edge_volume(const em_mesh* m, const double* x, const double* n, double* vol, void* ws, cudaStream_t s);
+int edge_residual(const em_mesh* m, const double* F, const double* n, const double* bnormal, double* res, void* ws,
+                  cudaStream_t s);
 int csr_fwd(const em_mesh* m, const double* x, double* n, double* vol, double* bnormal, void* ws, cudaStream_t s);
 
 int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const int32_t* elem2edge, int64_t n_edges,

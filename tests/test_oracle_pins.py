@@ -397,3 +397,37 @@ def test_sampled_oracle_equals_full(builder):
     assert np.abs(sv - v).max() <= 1e-15 * m.h ** m.dim
     assert np.abs(sb - full_b).max() <= 1e-15 * m.h ** (m.dim - 1)
     assert np.abs(sg - g).max() <= 1e-14 * np.abs(g).max()
+
+
+# ----------------------------------------------------------------------------
+# edge-loop residual (Sec. 2): what the metrics are for
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("builder", [
+    lambda: meshgen.tri_square(10, jitter=0.3, seed=51),
+    lambda: meshgen.kuhn_cube(5, jitter=0.3, seed=52),
+    lambda: meshgen.kuhn_cube(4, jitter=0.2, seed=53, offset=1000.0),
+])
+def test_edge_residual_linear_exactness(builder):
+    """For a linear flux F = A x + f0 the central-flux edge loop reproduces
+    V_j div F = V_j tr(A) at every interior node (a consequence of closure and
+    of sum_k 1/2 (x_k - x_j) (x) n_jk = V_j I, not of the residual's own code);
+    a constant flux gives zero there; and the edge fluxes cancel in the total,
+    leaving sum_b F_b . bnormal_b."""
+    m = builder()
+    d = m.dim
+    t, n, v, b = _metrics(m)
+    rng = np.random.Generator(np.random.PCG64(77))
+    A = rng.standard_normal((d, d))
+    f0 = rng.standard_normal(d)
+    xr = m.x - m.x.mean(axis=0)                  # keep F of order one on the offset grid
+    F = xr @ A.T + f0
+    r = oracle.edge_residual(d, t, n, F, b)
+    inner = np.ones(m.n_nodes, bool)
+    inner[t.bnode] = False
+    scale = np.abs(F).max() * m.h ** (d - 1)
+    assert np.abs(r[inner] - v[inner] * np.trace(A)).max() <= 1e-12 * scale
+    r0 = oracle.edge_residual(d, t, n, np.tile(f0, (m.n_nodes, 1)), b)
+    assert np.abs(r0[inner]).max() <= 1e-12 * np.abs(f0).max() * m.h ** (d - 1)
+    total = float(np.sum(F[t.bnode] * b))
+    assert abs(r.sum() - total) <= 1e-11 * scale * m.n_nodes
