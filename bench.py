@@ -439,6 +439,7 @@ def run_ours(args):
         if have_gather:
             cand += [(p_, q_) for p_ in ("gather", "tiled") for q_ in ("fp64", "dw", "mixed")]
         cand += [("fwd:" + p_, q_) for p_, q_ in (("atomic", "fp64"), ("atomic", "mixed"), ("csr", "fp64"))]
+        cand += [("traditional:atomic", "fp64")]   # the paper's comparison algorithm, n_jk only
         if have_gather:
             cand += [("fwd:tiled", q_) for q_ in ("fp64", "dw", "mixed")]
         fwd_bytes = algorithmic_bytes(m, topo, "fwd", path)
@@ -454,7 +455,9 @@ def run_ours(args):
                                                         use_cache=False)
                     forms["fwd:tiled tile_nodes"] = {"tile_nodes": fwd_tile, "sweep_ms": fsweep}
                 def fstep():
-                    if pth.startswith("fwd:"):
+                    if pth.startswith("traditional:"):
+                        api.edge_areas_traditional(topo, x, out=outs[0])
+                    elif pth.startswith("fwd:"):
                         api.edge_metrics(topo, x, pr, pth[4:], out=outs[:3])
                     elif pth in ("gather", "tiled"):
                         api.edge_metrics_fused(topo, x, w, c, pr, out=outs, path=pth)
@@ -475,7 +478,7 @@ def run_ours(args):
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms = a.elapsed_time(b) / reps
-                nb = fwd_bytes if pth.startswith("fwd:") else step_bytes
+                nb = fwd_bytes if pth.startswith(("fwd:", "traditional:")) else step_bytes
                 forms[f"{pth}/{pr}"] = {"ms_per_step": round(ms, 4), "elements_per_s": m.n_elems / (ms * 1e-3),
                                         "algorithmic_GBs": nb / (ms * 1e-3) / 1e9,
                                         "roofline_frac": nb / (ms * 1e-3) / 1e9 / peak}

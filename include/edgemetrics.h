@@ -273,6 +273,18 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path,
 int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, double* vol,
                    void* ws, size_t* ws_bytes, void* stream);
 
+/* em_edge_areas_traditional -- the directed-area vectors n_jk by the
+ * TRADITIONAL construction the paper compares against (Sec. 3.1): in every
+ * element, for every element edge, the dual-face part spanned by the edge
+ * midpoint, the centroids of the two element faces that contain the edge and
+ * the element centroid (2D: edge midpoint to element centroid), directed from
+ * the lower to the higher node id; FP64, one thread per element, FP64 atomic
+ * accumulation (so the summation order, and the last bits, vary from run to
+ * run).  Equals em_edge_metrics' n_edge up to rounding.  Provided to measure
+ * the paper's comparison on this GPU; n_edge [n_edges][dim] is overwritten.
+ * Needs mesh->elems and mesh->elem2edge. */
+int em_edge_areas_traditional(const em_mesh* mesh, const double* x, double* n_edge, void* stream);
+
 /* em_edge_residual -- the edge-loop residual of the edge-based
  * discretization (Sec. 2) for a given nodal flux F [n_nodes][dim]:
  *   res_j = sum_{edges {j,k}} phi_jk - sum_{edges {i,j}} phi_ij + F_j . bnormal_j,

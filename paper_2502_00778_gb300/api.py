@@ -259,6 +259,17 @@ def edge_volume(topo: Topology, x, n_edge):
     return v
 
 
+def edge_areas_traditional(topo: Topology, x, out=None):
+    """n_jk by the traditional dual-face construction (Sec. 3.1), FP64 atomics."""
+    L = load()
+    _require_cuda(x)
+    x = x.contiguous().to(torch.float64)
+    n = out if out is not None else torch.empty((topo.n_edges, topo.dim), dtype=torch.float64, device=x.device)
+    m, mr = _mesh_ref(topo)
+    check(L.em_edge_areas_traditional(mr, _ptr(x), _ptr(n), _stream()))
+    return n
+
+
 def edge_residual(topo: Topology, F, n_edge, bnormal):
     """Edge-loop residual with central fluxes (Sec. 2) for nodal fluxes F."""
     L = load()

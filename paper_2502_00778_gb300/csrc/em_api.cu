@@ -183,6 +183,16 @@ int em_edge_volume(const em_mesh* mesh, const double* x, const double* n_edge, d
     return st == EM_OK ? ok() : st;
 }
 
+int em_edge_areas_traditional(const em_mesh* mesh, const double* x, double* n_edge, void* stream) {
+    if (!mesh) return fail(EM_ERR_ARG, "mesh is NULL");
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(EM_ERR_ARG, "mesh->dim must be 2 or 3");
+    if (mesh->n_elems <= 0 || mesh->n_edges <= 0 || !mesh->elems || !mesh->elem2edge)
+        return fail(EM_ERR_ARG, "mesh needs elems and elem2edge");
+    if (!x || !n_edge) return fail(EM_ERR_ARG, "x and n_edge must not be NULL");
+    int st = traditional_areas(mesh, x, n_edge, as_stream(stream));
+    return st == EM_OK ? ok() : st;
+}
+
 int em_edge_residual(const em_mesh* mesh, const double* F, const double* n_edge, const double* bnormal, double* res,
                      void* ws, size_t* ws_bytes, void* stream) {
     if (!mesh) return fail(EM_ERR_ARG, "mesh is NULL");

@@ -57,6 +57,69 @@ __device__ __forceinline__ void comp_add(float* hi, float* lo, float v) {
     atomicAdd(lo, err);
 }
 
+// ---- the traditional dual-face construction (Sec. 3.1), for comparison ------
+// Per element and per element edge {j,k} (j the lower global id): the part of
+// the edge's dual face inside the element, built from the edge midpoint, the
+// centroids of the element's two faces that contain the edge and the element
+// centroid (3D: two triangles; 2D: the segment from the edge midpoint to the
+// element centroid), each directed from j to k, added with FP64 atomics.  In
+// element-local coordinates (the first stored node subtracted).
+__global__ void k_trad_atomic3(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                               const double* __restrict__ x, double* __restrict__ n) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        const int4 v = reinterpret_cast<const int4*>(elems)[E];
+        const d3 x0 = ld3(x, v.x);
+        d3 p[4] = {mk(0.0, 0.0, 0.0), ld3(x, v.y) - x0, ld3(x, v.z) - x0, ld3(x, v.w) - x0};
+        const int gid[4] = {v.x, v.y, v.z, v.w};
+        const d3 xE = 0.25 * (p[0] + p[1] + p[2] + p[3]);
+#pragma unroll
+        for (int l = 0; l < 6; l++) {
+            const int a = c_le3a[l][0], b = c_le3a[l][1];
+            const int jl = gid[a] < gid[b] ? a : b, kl = jl == a ? b : a;
+            const int ll = (a == 0 || b == 0) ? (a == 1 || b == 1 ? 2 : 1) : 0;
+            const int rl = 6 - a - b - ll;
+            const d3 djk = p[kl] - p[jl];
+            const d3 xm = 0.5 * (p[jl] + p[kl]);
+            const d3 xL = (1.0 / 3.0) * (p[jl] + p[ll] + p[kl]);
+            const d3 xR = (1.0 / 3.0) * (p[jl] + p[rl] + p[kl]);
+            const d3 Em = xE - xm;
+            d3 nEL = 0.5 * cross(Em, xL - xm), nER = 0.5 * cross(xR - xm, Em);
+            if (dot(nEL, djk) < 0) nEL = -1.0 * nEL;
+            if (dot(nER, djk) < 0) nER = -1.0 * nER;
+            const int64_t e = e2e[E * 6 + l];
+            atomicAdd(n + 3 * e, nEL.x + nER.x);
+            atomicAdd(n + 3 * e + 1, nEL.y + nER.y);
+            atomicAdd(n + 3 * e + 2, nEL.z + nER.z);
+        }
+    }
+}
+
+__global__ void k_trad_atomic2(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
+                               const double* __restrict__ x, double* __restrict__ n) {
+    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < ne; E += int64_t(gridDim.x) * blockDim.x) {
+        const int4 v = reinterpret_cast<const int4*>(elems)[E];
+        const int gid[3] = {v.x, v.y, v.z};
+        const double x0 = x[2 * int64_t(v.x)], y0 = x[2 * int64_t(v.x) + 1];
+        double px[3] = {0.0, x[2 * int64_t(v.y)] - x0, x[2 * int64_t(v.z)] - x0};
+        double py[3] = {0.0, x[2 * int64_t(v.y) + 1] - y0, x[2 * int64_t(v.z) + 1] - y0};
+        const double xE = (px[0] + px[1] + px[2]) * (1.0 / 3.0), yE = (py[0] + py[1] + py[2]) * (1.0 / 3.0);
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            const int a = c_le2a[l][0], b = c_le2a[l][1];
+            const int jl = gid[a] < gid[b] ? a : b, kl = jl == a ? b : a;
+            const double xm = 0.5 * (px[jl] + px[kl]), ym = 0.5 * (py[jl] + py[kl]);
+            double nx = ym - yE, ny = xE - xm;
+            if (nx * (px[kl] - px[jl]) + ny * (py[kl] - py[jl]) < 0) {
+                nx = -nx;
+                ny = -ny;
+            }
+            const int64_t e = e2e[E * 3 + l];
+            atomicAdd(n + 2 * e, nx);
+            atomicAdd(n + 2 * e + 1, ny);
+        }
+    }
+}
+
 // ---- forward, 3D ----------------------------------------------------------
 template <int PREC>
 __global__ void k_fwd_atomic3(int64_t ne, const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
@@ -357,6 +420,17 @@ __global__ void k_bnd_adj_atomic(int64_t nbf, const int32_t* __restrict__ bface,
 }
 
 }  // namespace
+
+int traditional_areas(const em_mesh* m, const double* x, double* n, cudaStream_t s) {
+    const int T = 256;
+    EM_CUDA_TRY(cudaMemsetAsync(n, 0, sizeof(double) * m->n_edges * m->dim, s));
+    const unsigned G = grid_for(m->n_elems, T, int64_t(num_sms()) * 16);
+    if (m->dim == 3) k_trad_atomic3<<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, n);
+    else k_trad_atomic2<<<G, T, 0, s>>>(m->n_elems, m->elems, m->elem2edge, x, n);
+    note_launches(1);
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
 
 size_t atomic_fwd_ws_bytes(const em_mesh* m, int prec) {
     WsLayout L(nullptr);

@@ -32,6 +32,7 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
 size_t csr_fwd_ws_bytes(const em_mesh* m);
 size_t edge_volume_ws_bytes(const em_mesh* m);
 int edge_volume(const em_mesh* m, const double* x, const double* n, double* vol, void* ws, cudaStream_t s);
+int traditional_areas(const em_mesh* m, const double* x, double* n, cudaStream_t s);
 int edge_residual(const em_mesh* m, const double* F, const double* n, const double* bnormal, double* res, void* ws,
                   cudaStream_t s);
 int csr_fwd(const em_mesh* m, const double* x, double* n, double* vol, double* bnormal, void* ws, cudaStream_t s);

@@ -75,3 +75,18 @@ def test_autograd_function(name="kuhn5"):
     L.backward()
     rg = oracle.adjoint(m.dim, m.x, m.elems, oracle_topo(name), w, c)
     assert_close_g(xr.grad.cpu().numpy(), rg)
+
+
+@pytest.mark.parametrize("name", list(SMALL_MESHES))
+def test_traditional_dual_faces(name):
+    """The traditional dual-face construction on the GPU (the paper's
+    comparison algorithm) against the oracle's, and against the proposed
+    formula's n_jk, which it equals up to rounding."""
+    from paper_2502_00778_gb300 import api
+    m = mesh(name)
+    x = torch.from_numpy(m.x).to(DEV)
+    topo = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+    nt = api.edge_areas_traditional(topo, x).cpu().numpy()
+    assert_close_n(nt, oracle.traditional(m.dim, m.x, m.elems, oracle_topo(name)), m, "traditional n")
+    rn, _, _ = oracle_fwd(name)
+    assert_close_n(nt, rn, m, "traditional vs proposed n")
