@@ -53,13 +53,13 @@ def lib():
             L.or_closure.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _f64p, _i64, _i32p, _f64p]
             L.or_adjoint.restype = None
             L.or_adjoint.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i32p, _i64, _i32p, _i64, _i32p,
-                                     _f64p, _f64p, _f64p]
+                                     _f64p, _f64p, _f64p, _f64p]
             L.or_loss_subset.restype = ctypes.c_double
             L.or_loss_subset.argtypes = [ctypes.c_int, _f64p, _i32p, _i32p, _i64, _i64p, _i64, _i32p, _i32p,
-                                         _i64, _i64p, _f64p, _f64p]
+                                         _i64, _i64p, _f64p, _f64p, _f64p]
             L.or_fd_gradient.restype = None
             L.or_fd_gradient.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i32p, _i64, _i32p, _i64, _i32p,
-                                         _f64p, _f64p, _i64, _i64p, ctypes.c_double, _f64p]
+                                         _f64p, _f64p, _f64p, _i64, _i64p, ctypes.c_double, _f64p]
             L.or_sample.restype = None
             L.or_sample.argtypes = [ctypes.c_int, _i64, _f64p, _i64, _i32p, _i64, _i32p, _i32p, _f64p, _i64, _i32p,
                                     _f64p, _f64p, ctypes.c_uint64, _f64p]
@@ -187,44 +187,60 @@ def closure(dim, x, topo, n_edge):
     return a
 
 
-def adjoint(dim, x, elems, topo, w, c):
+def _bw_node(topo, n_nodes, dim, bw):
+    """Boundary-normal weights given per boundary node (topo.bnode order) as a
+    per-node array, zero at interior nodes; None stays None."""
+    if bw is None:
+        return None
+    out = np.zeros((n_nodes, dim))
+    out[np.asarray(topo.bnode)] = np.asarray(bw, dtype=np.float64).reshape(-1, dim)
+    return out
+
+
+def adjoint(dim, x, elems, topo, w, c, bw=None):
+    """dL/dx for L = sum_e w_e.n_e + sum_i c_i V_i (+ sum_b bw_b.bnormal_b)."""
     x = _c(x, np.float64)
     elems = _c(elems, np.int32)
     w = _c(w, np.float64)
     c = _c(c, np.float64)
+    bn = _bw_node(topo, x.shape[0], dim, bw)
     g = np.empty((x.shape[0], dim))
     lib().or_adjoint(dim, x.shape[0], _p(x, _f64p), elems.shape[0], _p(elems, _i32p), _p(topo.elem2edge, _i32p),
                      topo.n_edges, _p(topo.edges, _i32p), topo.bface.shape[0], _p(topo.bface, _i32p),
-                     _p(w, _f64p), _p(c, _f64p), _p(g, _f64p))
+                     _p(w, _f64p), _p(c, _f64p), None if bn is None else _p(bn, _f64p), _p(g, _f64p))
     return g
 
 
-def loss_subset(dim, x, elems, topo, sel, bsel, w, c):
+def loss_subset(dim, x, elems, topo, sel, bsel, w, c, bw=None):
     x = _c(x, np.float64)
     elems = _c(elems, np.int32)
     sel = _c(sel, np.int64)
     bsel = _c(bsel, np.int64)
     w = _c(w, np.float64)
     c = _c(c, np.float64)
+    bn = _bw_node(topo, x.shape[0], dim, bw)
     return lib().or_loss_subset(dim, _p(x, _f64p), _p(elems, _i32p), _p(topo.elem2edge, _i32p), sel.shape[0],
                                 _p(sel, _i64p), topo.n_edges, _p(topo.edges, _i32p), _p(topo.bface, _i32p),
-                                bsel.shape[0], _p(bsel, _i64p), _p(w, _f64p), _p(c, _f64p))
+                                bsel.shape[0], _p(bsel, _i64p), _p(w, _f64p), _p(c, _f64p),
+                                None if bn is None else _p(bn, _f64p))
 
 
-def loss(dim, x, elems, topo, w, c):
-    return loss_subset(dim, x, elems, topo, np.arange(elems.shape[0]), np.arange(topo.bface.shape[0]), w, c)
+def loss(dim, x, elems, topo, w, c, bw=None):
+    return loss_subset(dim, x, elems, topo, np.arange(elems.shape[0]), np.arange(topo.bface.shape[0]), w, c, bw)
 
 
-def fd_gradient(dim, x, elems, topo, w, c, nodes, delta):
+def fd_gradient(dim, x, elems, topo, w, c, nodes, delta, bw=None):
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     elems = _c(elems, np.int32)
     w = _c(w, np.float64)
     c = _c(c, np.float64)
     nodes = _c(nodes, np.int64)
+    bn = _bw_node(topo, x.shape[0], dim, bw)
     g = np.empty((nodes.shape[0], dim))
     lib().or_fd_gradient(dim, x.shape[0], _p(x, _f64p), elems.shape[0], _p(elems, _i32p), _p(topo.elem2edge, _i32p),
                          topo.n_edges, _p(topo.edges, _i32p), topo.bface.shape[0], _p(topo.bface, _i32p),
-                         _p(w, _f64p), _p(c, _f64p), nodes.shape[0], _p(nodes, _i64p), float(delta), _p(g, _f64p))
+                         _p(w, _f64p), _p(c, _f64p), None if bn is None else _p(bn, _f64p), nodes.shape[0],
+                         _p(nodes, _i64p), float(delta), _p(g, _f64p))
     return g
 
 

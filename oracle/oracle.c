@@ -28,6 +28,7 @@
  *                       (Sec. 2): central flux 1/2 (F_j + F_k).n_jk out of
  *                       j and into k, plus F_j.bnormal_j at boundary nodes
  *   or_adjoint          analytic gradient of L = sum_e w_e.n_e + sum_i c_i V_i
+ *                       (+ sum_b bw_b.bnormal_b when boundary weights are given)
  *   or_loss_subset      L restricted to chosen elements / boundary faces
  *   or_fd_gradient      patch-local central differences of L
  *
@@ -514,17 +515,37 @@ static void bface_edge_weight(int dim, int64_t nedges, const int32_t* edges, con
 }
 
 /* g[nv*dim] overwritten with dL/dx */
+/* K_B = w_B / (D(D+1)) + (1/D) sum_{b in B} bw_b: the vector that multiplies a
+ * boundary face's n_B in L (its edges' n_jk corrections and, with boundary-
+ * normal weights bw given per node, the 1/D n_B of its nodes' bnormal) */
+static void bface_coeff(int dim, int64_t nedges, const int32_t* edges, const int32_t* f, const double* w,
+                        const double* bw_node, double* K) {
+    double wB[3];
+    bface_edge_weight(dim, nedges, edges, f, w, wB);
+    for (int q = 0; q < dim; q++) {
+        double bs = 0;
+        for (int a = 0; a < dim; a++) bs += bw_node[dim * (int64_t)f[a] + q];
+        K[q] = wB[q] / (dim * (dim + 1.0)) + bs / dim;
+    }
+}
+
 void or_adjoint(int dim, int64_t nv, const double* x, int64_t ne, const int32_t* elems, const int32_t* elem2edge,
                 int64_t nedges, const int32_t* edges, int64_t nb, const int32_t* bface,
-                const double* w, const double* c, double* g) {
+                const double* w, const double* c, const double* bw_node, double* g) {
     const int nl = nloc_edges(dim);
     memset(g, 0, sizeof(double) * (size_t)(nv * dim));
     for (int64_t E = 0; E < ne; E++) elem_grad(dim, x, elems + 4 * E, elem2edge + nl * E, w, c, g);
     const double beta = 1.0 / (dim * (dim + 1.0));
     for (int64_t B = 0; B < nb; B++) {
-        double wB[3];
-        bface_edge_weight(dim, nedges, edges, bface + dim * B, w, wB);
-        bface_grad(dim, x, bface + dim * B, wB, beta, g);
+        if (bw_node) {
+            double K[3];
+            bface_coeff(dim, nedges, edges, bface + dim * B, w, bw_node, K);
+            bface_grad(dim, x, bface + dim * B, K, 1.0, g);
+        } else {
+            double wB[3];
+            bface_edge_weight(dim, nedges, edges, bface + dim * B, w, wB);
+            bface_grad(dim, x, bface + dim * B, wB, beta, g);
+        }
     }
 }
 
@@ -532,7 +553,7 @@ void or_adjoint(int dim, int64_t nv, const double* x, int64_t ne, const int32_t*
  * or_direct, contribution by contribution) */
 double or_loss_subset(int dim, const double* x, const int32_t* elems, const int32_t* elem2edge,
                       int64_t nsel, const int64_t* sel, int64_t nedges, const int32_t* edges, const int32_t* bface,
-                      int64_t nbsel, const int64_t* bsel, const double* w, const double* c) {
+                      int64_t nbsel, const int64_t* bsel, const double* w, const double* c, const double* bw_node) {
     const int nl = nloc_edges(dim);
     const int (*le)[2] = local_edges(dim);
     const double alpha = 2.0 / (dim * (dim + 1.0));
@@ -553,8 +574,13 @@ double or_loss_subset(int dim, const double* x, const int32_t* elems, const int3
         const int32_t* f = bface + dim * bsel[s];
         double nB[3] = {0, 0, 0}, wB[3];
         face_area_vector(dim, x, f, nB);
-        bface_edge_weight(dim, nedges, edges, f, w, wB);
-        L += beta * dot(wB, nB, dim);
+        if (bw_node) {
+            bface_coeff(dim, nedges, edges, f, w, bw_node, wB);
+            L += dot(wB, nB, dim);
+        } else {
+            bface_edge_weight(dim, nedges, edges, f, w, wB);
+            L += beta * dot(wB, nB, dim);
+        }
     }
     return L;
 }
@@ -564,7 +590,8 @@ double or_loss_subset(int dim, const double* x, const int32_t* elems, const int3
  * place and restored.  g_fd[nn*dim] overwritten. */
 void or_fd_gradient(int dim, int64_t nv, double* x, int64_t ne, const int32_t* elems, const int32_t* elem2edge,
                     int64_t nedges, const int32_t* edges, int64_t nb, const int32_t* bface,
-                    const double* w, const double* c, int64_t nn, const int64_t* nodes, double delta, double* g_fd) {
+                    const double* w, const double* c, const double* bw_node, int64_t nn, const int64_t* nodes,
+                    double delta, double* g_fd) {
     int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nv > 0 ? nv : 1));
     for (int64_t v = 0; v < nv; v++) pos[v] = -1;
     for (int64_t i = 0; i < nn; i++) pos[nodes[i]] = i;
@@ -585,10 +612,10 @@ void or_fd_gradient(int dim, int64_t nv, double* x, int64_t ne, const int32_t* e
             double x0 = x[dim * v + q];
             x[dim * v + q] = x0 + delta;
             double Lp = or_loss_subset(dim, x, elems, elem2edge, ecnt[i + 1] - ecnt[i], elist + ecnt[i], nedges, edges, bface,
-                                       bcnt[i + 1] - bcnt[i], blist + bcnt[i], w, c);
+                                       bcnt[i + 1] - bcnt[i], blist + bcnt[i], w, c, bw_node);
             x[dim * v + q] = x0 - delta;
             double Lm = or_loss_subset(dim, x, elems, elem2edge, ecnt[i + 1] - ecnt[i], elist + ecnt[i], nedges, edges, bface,
-                                       bcnt[i + 1] - bcnt[i], blist + bcnt[i], w, c);
+                                       bcnt[i + 1] - bcnt[i], blist + bcnt[i], w, c, bw_node);
             x[dim * v + q] = x0;
             g_fd[dim * i + q] = (Lp - Lm) / (2.0 * delta);
         }

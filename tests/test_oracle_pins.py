@@ -431,3 +431,41 @@ def test_edge_residual_linear_exactness(builder):
     assert np.abs(r0[inner]).max() <= 1e-12 * np.abs(f0).max() * m.h ** (d - 1)
     total = float(np.sum(F[t.bnode] * b))
     assert abs(r.sum() - total) <= 1e-11 * scale * m.n_nodes
+
+
+# ----------------------------------------------------------------------------
+# adjoint with boundary-normal weights: L += sum_b bw_b . bnormal_b
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("builder", [
+    lambda: meshgen.tri_square(5, jitter=0.3, seed=61),
+    lambda: meshgen.kuhn_cube(3, jitter=0.3, seed=62),
+    lambda: meshgen.single_simplex(3),
+])
+def test_adjoint_with_boundary_weights(builder):
+    """The boundary-weight part of L equals sum_b bw_b . bnormal_b with the
+    forward's own boundary normals (a separate loop), and the analytic
+    gradient matches full-loss central differences."""
+    m = builder()
+    d = m.dim
+    t = oracle.topology(d, m.elems, m.x)
+    w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, d, seed=8)
+    rng = np.random.Generator(np.random.PCG64(63))
+    bw = rng.standard_normal((len(t.bnode), d))
+    n, v, b = oracle.direct(d, m.x, m.elems, t)
+    L0 = oracle.loss(d, m.x, m.elems, t, w, c)
+    L1 = oracle.loss(d, m.x, m.elems, t, w, c, bw)
+    assert abs((L1 - L0) - np.sum(bw * b)) <= 1e-13 * np.abs(bw * b).sum()
+    g = oracle.adjoint(d, m.x, m.elems, t, w, c, bw)
+    g0 = oracle.adjoint(d, m.x, m.elems, t, w, c)
+    assert np.abs(g - g0).max() > 0                    # the boundary weights do move the gradient
+    delta = 1e-6 * (m.h if m.n_elems > 1 else 1.0)
+    gfd = np.zeros_like(g)
+    for i in range(m.n_nodes):
+        for q in range(d):
+            xp = m.x.copy(); xp[i, q] += delta
+            xm = m.x.copy(); xm[i, q] -= delta
+            gfd[i, q] = (oracle.loss(d, xp, m.elems, t, w, c, bw) - oracle.loss(d, xm, m.elems, t, w, c, bw)) / (2 * delta)
+    assert np.abs(g - gfd).max() <= 1e-7 * np.abs(g).max()
+    gp = oracle.fd_gradient(d, m.x, m.elems, t, w, c, np.arange(m.n_nodes), delta, bw)
+    assert np.abs(g - gp).max() <= 1e-7 * np.abs(g).max()
