@@ -243,20 +243,25 @@ int em_edge_metrics(const em_mesh* mesh, int precision, int path,
                     void* ws, size_t* ws_bytes, void* stream);
 
 /* em_edge_metrics_adjoint -- grad_x [n_nodes][dim] (overwritten) =
- * d/dx ( sum_e w[e] . n_e + sum_i c[i] V_i ), w [n_edges][dim], c [n_nodes]
- * (c may be NULL: treated as zero).  Boundary dual-face normals are not part
- * of L.  Supported pairs: ATOMIC with FP64 or MIXED; GATHER with FP64, DW,
- * MIXED. */
+ * d/dx ( sum_e w[e] . n_e + sum_i c[i] V_i + sum_b bw[b] . bnormal_b ),
+ * w [n_edges][dim], c [n_nodes] (NULL: zero), bw [n_bnodes][dim] weights of
+ * the boundary dual-face normals in mesh->bnode order (NULL: no such term;
+ * not supported on the GATHER path).  The derivative of the paper's
+ * equations (Eq. efficient_njk_formula_general_D with the boundary
+ * correction, Sec. 4.2, Sec. 3.2.3).  Supported pairs: ATOMIC with FP64 or
+ * MIXED; GATHER and TILED with FP64, DW, MIXED.  The workspace holds a
+ * node -> boundary-node map used when bw is given. */
 int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path,
-                            const double* x, const double* w, const double* c,
+                            const double* x, const double* w, const double* c, const double* bw,
                             double* grad_x,
                             void* ws, size_t* ws_bytes, void* stream);
 
 /* em_edge_metrics_fused -- forward outputs and the adjoint in one pass over
  * the grid (the adjoint does not depend on the forward outputs).  path:
- * EM_PATH_GATHER or EM_PATH_TILED (FP64, DW, MIXED). */
+ * EM_PATH_GATHER or EM_PATH_TILED (FP64, DW, MIXED); w, c, bw as in
+ * em_edge_metrics_adjoint (bw only on the TILED path). */
 int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path,
-                          const double* x, const double* w, const double* c,
+                          const double* x, const double* w, const double* c, const double* bw,
                           double* n_edge, double* vol, double* bnormal, double* grad_x,
                           void* ws, size_t* ws_bytes, void* stream);
 

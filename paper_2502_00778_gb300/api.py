@@ -196,34 +196,41 @@ def edge_metrics(topo: Topology, x: torch.Tensor, precision: str = "fp64", path:
     return n, v, b
 
 
-def edge_metrics_adjoint(topo: Topology, x, w, c=None, precision: str = "fp64", path: str = "atomic", out=None):
-    """grad_x = d/dx (sum w.n + sum c V), float64 [Nv, dim]."""
+def edge_metrics_adjoint(topo: Topology, x, w, c=None, precision: str = "fp64", path: str = "atomic", out=None,
+                         bw=None):
+    """grad_x = d/dx (sum w.n + sum c V + sum bw.bnormal), float64 [Nv, dim];
+    bw (boundary-normal weights, [n_bnodes, dim] in topo.bnode order) is
+    optional and supported on the atomic and tiled paths."""
     L = load()
-    _require_cuda(x, w, c)
+    _require_cuda(x, w, c, bw)
     x = x.contiguous().to(torch.float64)
     w = w.contiguous().to(torch.float64)
     c = c.contiguous().to(torch.float64) if c is not None else None
+    bw = bw.contiguous().to(torch.float64) if bw is not None else None
     g = out if out is not None else torch.empty((topo.n_nodes, topo.dim), dtype=torch.float64, device=x.device)
     m, mr = _mesh_ref(topo)
     wsb = ctypes.c_size_t(0)
     null = ctypes.c_void_p(0)
     pr, pa = PREC[precision], PATH[path]
-    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(g), null, ctypes.byref(wsb),
-                                    _stream()))
+    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(bw), _ptr(g), null,
+                                    ctypes.byref(wsb), _stream()))
     ws = workspace.get(wsb.value, x.device)
-    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(g), _ptr(ws), ctypes.byref(wsb),
-                                    _stream()))
+    check(L.em_edge_metrics_adjoint(mr, pr, pa, _ptr(x), _ptr(w), _ptr(c), _ptr(bw), _ptr(g), _ptr(ws),
+                                    ctypes.byref(wsb), _stream()))
     return g
 
 
-def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", out=None, path: str = "gather"):
+def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", out=None, path: str = "gather",
+                       bw=None):
     """Forward outputs and the adjoint in one pass (plan required; path
-    "gather" = deterministic ordered gather, "tiled" = shared-memory scatter)."""
+    "gather" = deterministic ordered gather, "tiled" = shared-memory scatter;
+    bw as in edge_metrics_adjoint, tiled path only)."""
     L = load()
-    _require_cuda(x, w, c)
+    _require_cuda(x, w, c, bw)
     x = x.contiguous().to(torch.float64)
     w = w.contiguous().to(torch.float64)
     c = c.contiguous().to(torch.float64) if c is not None else None
+    bw = bw.contiguous().to(torch.float64) if bw is not None else None
     dim, dev = topo.dim, x.device
     if out is None:
         n = torch.empty((topo.n_edges, dim), dtype=torch.float64, device=dev)
@@ -236,7 +243,7 @@ def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", ou
     wsb = ctypes.c_size_t(0)
     null = ctypes.c_void_p(0)
     pr, pa = PREC[precision], PATH[path]
-    args = (_ptr(x), _ptr(w), _ptr(c), _ptr(n), _ptr(v), _ptr(b), _ptr(g))
+    args = (_ptr(x), _ptr(w), _ptr(c), _ptr(bw), _ptr(n), _ptr(v), _ptr(b), _ptr(g))
     check(L.em_edge_metrics_fused(mr, pr, pa, *args, null, ctypes.byref(wsb), _stream()))
     ws = workspace.get(wsb.value, dev)
     check(L.em_edge_metrics_fused(mr, pr, pa, *args, _ptr(ws), ctypes.byref(wsb), _stream()))
@@ -307,15 +314,16 @@ def check_elements(dim: int, elems: torch.Tensor, x: torch.Tensor):
 class EdgeMetrics(torch.autograd.Function):
     """(n_edge, vol, bnormal) = EdgeMetrics.apply(x, topo, precision, path).
 
-    backward calls the adjoint kernel with w = grad(n_edge), c = grad(vol);
-    the gradient through bnormal is not propagated (it is not part of L)."""
+    backward calls the adjoint kernel with w = grad(n_edge), c = grad(vol)
+    and bw = grad(bnormal) (the ordered-gather path takes its adjoint on the
+    tiled path when bnormal carries a gradient)."""
 
     @staticmethod
     def forward(ctx, x, topo, precision="fp64", path="atomic"):
         ctx.topo, ctx.precision, ctx.path = topo, precision, path
         ctx.save_for_backward(x)
+        ctx.set_materialize_grads(False)      # an unused output's gradient arrives as None
         n, v, b = edge_metrics(topo, x, precision, path)
-        ctx.mark_non_differentiable(b)
         return n, v, b
 
     @staticmethod
@@ -325,8 +333,10 @@ class EdgeMetrics(torch.autograd.Function):
         if gn is None:
             gn = torch.zeros((topo.n_edges, topo.dim), dtype=torch.float64, device=x.device)
         adj_path = ctx.path if ctx.path in ("atomic", "gather", "tiled") else "atomic"
+        if gb is not None and adj_path == "gather":
+            adj_path = "tiled"
         g = edge_metrics_adjoint(topo, x, gn, gv, ctx.precision if ctx.precision != "mixed_comp32" else "mixed",
-                                 adj_path)
+                                 adj_path, bw=gb)
         return g, None, None, None
 
 

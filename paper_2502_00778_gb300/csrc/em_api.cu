@@ -125,7 +125,8 @@ int em_edge_metrics(const em_mesh* mesh, int precision, int path, const double* 
 }
 
 int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path, const double* x, const double* w,
-                            const double* c, double* grad_x, void* ws, size_t* ws_bytes, void* stream) {
+                            const double* c, const double* bw, double* grad_x, void* ws, size_t* ws_bytes,
+                            void* stream) {
     EM_TRY(check_mesh(mesh));
     size_t need = 0;
     if (path == EM_PATH_ATOMIC) {
@@ -139,34 +140,49 @@ int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path, const 
     } else {
         return fail(EM_ERR_ARG, "adjoint supports the ATOMIC, GATHER and TILED paths");
     }
+    if (bw && path == EM_PATH_GATHER)
+        return fail(EM_ERR_ARG, "boundary-normal weights are supported by the TILED and ATOMIC paths");
+    const size_t bw_off = (need + 255) & ~size_t(255);
+    need = bw_off + bw_ws_bytes(mesh);
     bool query;
     EM_TRY(check_ws(ws, ws_bytes, need, &query));
     if (query) return ok();
     if (!x || !w || !grad_x) return fail(EM_ERR_ARG, "x, w and grad_x must not be NULL");
     cudaStream_t s = as_stream(stream);
+    BwAux aux;
+    EM_TRY(bw_prepare(mesh, bw, static_cast<char*>(ws) + bw_off, &aux, s));
     int st;
-    if (path == EM_PATH_ATOMIC) st = atomic_adj(mesh, precision, x, w, c, grad_x, s);
-    else
+    if (path == EM_PATH_ATOMIC) {
+        st = atomic_adj(mesh, precision, x, w, c, grad_x, s);
+        if (st == EM_OK) st = atomic_bw_adj(mesh, x, aux, grad_x, s);
+    } else {
         st = gather_run(mesh, precision, GATHER_ADJ | (path == EM_PATH_TILED ? GATHER_SCATTER : 0), x, w, c, nullptr,
-                        nullptr, nullptr, grad_x, ws, s);
+                        nullptr, nullptr, grad_x, ws, s, &aux);
+    }
     return st == EM_OK ? ok() : st;
 }
 
 int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path, const double* x, const double* w,
-                          const double* c, double* n_edge, double* vol, double* bnormal, double* grad_x, void* ws,
-                          size_t* ws_bytes, void* stream) {
+                          const double* c, const double* bw, double* n_edge, double* vol, double* bnormal,
+                          double* grad_x, void* ws, size_t* ws_bytes, void* stream) {
     EM_TRY(check_mesh(mesh));
     if (path != EM_PATH_GATHER && path != EM_PATH_TILED) return fail(EM_ERR_ARG, "fused pass: GATHER or TILED path");
     if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
         return fail(EM_ERR_ARG, "fused pass supports FP64, DW and MIXED");
     if (!mesh->plan) return fail(EM_ERR_ARG, "fused pass needs a plan from em_plan_build");
+    if (bw && path == EM_PATH_GATHER)
+        return fail(EM_ERR_ARG, "boundary-normal weights are supported by the TILED and ATOMIC paths");
+    const size_t bw_off = (gather_ws_bytes(mesh) + 255) & ~size_t(255);
     bool query;
-    EM_TRY(check_ws(ws, ws_bytes, gather_ws_bytes(mesh), &query));
+    EM_TRY(check_ws(ws, ws_bytes, bw_off + bw_ws_bytes(mesh), &query));
     if (query) return ok();
     if (!x || !w || !grad_x || !n_edge || !vol || (mesh->n_bnodes && !bnormal))
         return fail(EM_ERR_ARG, "fused pass needs x, w and all outputs");
+    cudaStream_t s = as_stream(stream);
+    BwAux aux;
+    EM_TRY(bw_prepare(mesh, bw, static_cast<char*>(ws) + bw_off, &aux, s));
     int st = gather_run(mesh, precision, GATHER_FWD | GATHER_ADJ | (path == EM_PATH_TILED ? GATHER_SCATTER : 0), x, w,
-                        c, n_edge, vol, bnormal, grad_x, ws, as_stream(stream));
+                        c, n_edge, vol, bnormal, grad_x, ws, s, &aux);
     return st == EM_OK ? ok() : st;
 }
 

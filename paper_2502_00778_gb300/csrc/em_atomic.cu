@@ -419,7 +419,83 @@ __global__ void k_bnd_adj_atomic(int64_t nbf, const int32_t* __restrict__ bface,
     }
 }
 
+// ---- boundary-normal weights: L += sum_b bw_b . bnormal_b ------------------
+// bnormal_b = (1/D) sum_{faces B at b} n_B, so each face adds the gradient of
+// K.n_B with K = (1/D) sum_{b in B} bw_b (3D n_B = 1/2 (x_q - x_p) x (x_r - x_p),
+// 2D n_B = (y_a - y_b, x_b - x_a)).  map[node] = boundary-node index or -1.
+__global__ void k_bw_map(int64_t nbn, const int32_t* __restrict__ bnode, int32_t* __restrict__ map) {
+    for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < nbn; b += int64_t(gridDim.x) * blockDim.x)
+        map[bnode[b]] = (int32_t)b;
+}
+// order-preserving key (upper word of |v|) of the largest |bw| component
+__global__ void k_bw_maxkey(int64_t m, const double* __restrict__ bw, unsigned* __restrict__ key) {
+    unsigned k = 0u;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        k = max(k, (unsigned)((unsigned long long)__double_as_longlong(bw[i]) >> 32) & 0x7fffffffu);
+    k = __reduce_max_sync(0xffffffffu, k);
+    if ((threadIdx.x & 31) == 0) atomicMax(key, k);
+}
+
+template <int DIM>
+__global__ void k_bnd_bw_adj(int64_t nbf, const int32_t* __restrict__ bface, const double* __restrict__ x,
+                             const double* __restrict__ bw, const int32_t* __restrict__ map, double* __restrict__ g) {
+    for (int64_t B = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; B < nbf; B += int64_t(gridDim.x) * blockDim.x) {
+        if (DIM == 3) {
+            const int p = bface[3 * B], q = bface[3 * B + 1], r = bface[3 * B + 2];
+            const d3 K = (1.0 / 3.0) * (ld3(bw, map[p]) + ld3(bw, map[q]) + ld3(bw, map[r]));
+            const d3 xp = ld3(x, p);
+            const d3 u = ld3(x, q) - xp, t = ld3(x, r) - xp;
+            const d3 gu = 0.5 * cross(t, K), gt = 0.5 * cross(K, u);
+            atomicAdd(g + 3 * int64_t(q), gu.x); atomicAdd(g + 3 * int64_t(q) + 1, gu.y); atomicAdd(g + 3 * int64_t(q) + 2, gu.z);
+            atomicAdd(g + 3 * int64_t(r), gt.x); atomicAdd(g + 3 * int64_t(r) + 1, gt.y); atomicAdd(g + 3 * int64_t(r) + 2, gt.z);
+            atomicAdd(g + 3 * int64_t(p), -(gu.x + gt.x));
+            atomicAdd(g + 3 * int64_t(p) + 1, -(gu.y + gt.y));
+            atomicAdd(g + 3 * int64_t(p) + 2, -(gu.z + gt.z));
+        } else {
+            const int a = bface[2 * B], b2 = bface[2 * B + 1];
+            const int64_t ia = map[a], ib = map[b2];
+            const double Kx = 0.5 * (bw[2 * ia] + bw[2 * ib]), Ky = 0.5 * (bw[2 * ia + 1] + bw[2 * ib + 1]);
+            atomicAdd(g + 2 * int64_t(b2), Ky); atomicAdd(g + 2 * int64_t(b2) + 1, -Kx);
+            atomicAdd(g + 2 * int64_t(a), -Ky); atomicAdd(g + 2 * int64_t(a) + 1, Kx);
+        }
+    }
+}
+
 }  // namespace
+
+size_t bw_ws_bytes(const em_mesh* m) { return 256 + sizeof(int32_t) * (size_t)m->n_nodes; }
+
+int bw_prepare(const em_mesh* m, const double* bw, void* ws, BwAux* aux, cudaStream_t s) {
+    unsigned* key = static_cast<unsigned*>(ws);
+    int32_t* map = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + 256);
+    aux->key = key;
+    aux->map = map;
+    aux->bw = bw;
+    if (!bw) return EM_OK;
+    if (m->n_bnodes && !m->bnode) return fail(EM_ERR_ARG, "boundary-normal weights need mesh->bnode");
+    const int T = 256;
+    EM_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, s));
+    EM_CUDA_TRY(cudaMemsetAsync(map, 0xff, sizeof(int32_t) * m->n_nodes, s));
+    if (m->n_bnodes) {
+        k_bw_map<<<grid_for(m->n_bnodes, T), T, 0, s>>>(m->n_bnodes, m->bnode, map);
+        k_bw_maxkey<<<grid_for(m->n_bnodes * m->dim, T), T, 0, s>>>(m->n_bnodes * m->dim, bw, key);
+        note_launches(2);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+int atomic_bw_adj(const em_mesh* m, const double* x, const BwAux& aux, double* g, cudaStream_t s) {
+    if (!aux.bw || !m->n_bfaces) return EM_OK;
+    const int T = 256;
+    if (m->dim == 3)
+        k_bnd_bw_adj<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, x, aux.bw, aux.map, g);
+    else
+        k_bnd_bw_adj<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, x, aux.bw, aux.map, g);
+    note_launches(1);
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
 
 int traditional_areas(const em_mesh* m, const double* x, double* n, cudaStream_t s) {
     const int T = 256;

@@ -170,6 +170,7 @@ struct TileArgs {
     int n_tiles;
     int val_e, val_v;          // largest edge / node valence of the grid
     int64_t tile_base;      // first tile handled by blockIdx.x == 0
+    BwAux bwa;              // boundary-normal weights of the adjoint (bwa.bw NULL: none)
 };
 
 template <int DIM, int PREC, int WHAT>
@@ -892,15 +893,18 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             sgv[0] = fx_sigma(32.0 * Lx * Lx * Ke, T, LO, HI);
             sgv[1] = fx_sigma(8.0 * Lx * Lx * Lx * Kv, T, LO, HI);
             sgv[2] = fx_sigma(32.0 * Lx * Lx * Kv, T, LO, HI);   // up to 3 boundary faces per element at a node
-            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx) *
-                                                    2.0 * Kv, T, LO, HI)
+            // boundary-normal weights: per face |1/2 t x K| <= 2 Lx max|bw| per component
+            const double Bm = ((WHAT & DO_ADJ) && A.bwa.bw) ? key_bound(*A.bwa.key) : 0.0;
+            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx +
+                                                 16.0 * Bm * Lx) * 2.0 * Kv, T, LO, HI)
                                      : 0;
         } else {
             sgv[0] = fx_sigma(8.0 * Lx * Ke, T, LO, HI);
             sgv[1] = fx_sigma(16.0 * Lx * Lx * Kv, T, LO, HI);
             sgv[2] = fx_sigma(8.0 * Lx * Kv, T, LO, HI);
-            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx) * 2.0 * Kv, T,
-                                                LO, HI)
+            const double Bm = ((WHAT & DO_ADJ) && A.bwa.bw) ? key_bound(*A.bwa.key) : 0.0;
+            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx + 4.0 * Bm) *
+                                                2.0 * Kv, T, LO, HI)
                                      : 0;
         }
     }
@@ -1156,11 +1160,31 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 for (int d = 0; d < 3; d++)
                     WB[d] = F::add(F::add(ws[f.e[0] * 3 + d], ws[f.e[1] * 3 + d]), ws[f.e[2] * 3 + d]);
                 const V f24 = F::cst(1.0 / 24.0);
+                // boundary-normal weights: K = 1/3 sum of bw at the face's nodes
+                V K[3];
+                const bool hasK = A.bwa.bw != nullptr;
+                if (hasK) {
+                    double Kd[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const int lv = f.v[k];
+                        const int64_t gv = lv < ti.n_own ? int64_t(ti.node0) + lv : int64_t(halo[lv - ti.n_own]);
+                        const int64_t b = A.bwa.map[gv];
+#pragma unroll
+                        for (int d = 0; d < 3; d++) Kd[d] += A.bwa.bw[3 * b + d];
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; d++) K[d] = F::from_double(Kd[d] / 3.0);
+                }
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
                     V gq = F::mul(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]), f24);
                     V gr = F::mul(F::det2(WB[d1], u[d2], WB[d2], u[d1]), f24);
+                    if (hasK) {
+                        gq = F::add(gq, F::half(F::det2(tt[d1], K[d2], tt[d2], K[d1])));
+                        gr = F::add(gr, F::half(F::det2(K[d1], u[d2], K[d2], u[d1])));
+                    }
                     if (f.v[1] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[1] * 3 + d, FX::q(gq, sg_g));
                     if (f.v[2] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[2] * 3 + d, FX::q(gr, sg_g));
                     if (f.v[0] < ti.n_own) acc_add<NL>(acc_g, sgs, f.v[0] * 3 + d, FX::q(F::sgn(F::add(gq, gr), -1.f), sg_g));
@@ -1182,6 +1206,19 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 const V f6 = F::cst(1.0 / 6.0);
                 V gx = F::mul(ws[f.e[0] * 2 + 1], f6);
                 V gy = F::sgn(F::mul(ws[f.e[0] * 2 + 0], f6), -1.f);
+                if (A.bwa.bw) {   // boundary-normal weights: K = 1/2 (bw_a + bw_b)
+                    double Kd[2] = {0.0, 0.0};
+#pragma unroll
+                    for (int k = 0; k < 2; k++) {
+                        const int lv = f.v[k];
+                        const int64_t gv = lv < ti.n_own ? int64_t(ti.node0) + lv : int64_t(halo[lv - ti.n_own]);
+                        const int64_t b = A.bwa.map[gv];
+                        Kd[0] += A.bwa.bw[2 * b];
+                        Kd[1] += A.bwa.bw[2 * b + 1];
+                    }
+                    gx = F::add(gx, F::from_double(0.5 * Kd[1]));
+                    gy = F::add(gy, F::from_double(-0.5 * Kd[0]));
+                }
                 if (f.v[1] < ti.n_own) {
                     acc_add<NL>(acc_g, sgs, f.v[1] * 2, FX::q(gx, sg_g));
                     acc_add<NL>(acc_g, sgs, f.v[1] * 2 + 1, FX::q(gy, sg_g));
@@ -1306,6 +1343,7 @@ __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs
     A.val_e = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_EDGE_VALENCE];
     A.val_v = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_NODE_VALENCE];
     A.tile_base = 0;
+    A.bwa = BwAux{nullptr, nullptr, nullptr};
 }
 
 template <int DIM, int PREC>
@@ -1408,7 +1446,7 @@ int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_p
 size_t gather_ws_bytes(const em_mesh*) { return 0; }
 
 int gather_run(const em_mesh* m, int prec, int what, const double* x, const double* w, const double* c, double* n,
-               double* vol, double* bnormal, double* g, void* ws, cudaStream_t s) {
+               double* vol, double* bnormal, double* g, void* ws, cudaStream_t s, const BwAux* bw) {
     (void)ws;
     const int64_t* pi = m->plan_info;
     if (pi[EM_PLAN_INFO_TILES] <= 0 || pi[EM_PLAN_INFO_CHECK] <= 0 || (size_t)pi[EM_PLAN_INFO_CHECK] > m->plan_bytes)
@@ -1431,6 +1469,9 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
     A.val_e = (int)(pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] : 64);
     A.val_v = (int)(pi[EM_PLAN_INFO_MAX_NODE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_NODE_VALENCE] : 64);
     A.tile_base = 0;
+    A.bwa = bw ? *bw : BwAux{nullptr, nullptr, nullptr};
+    if (A.bwa.bw && !(what & GATHER_SCATTER))
+        return fail(EM_ERR_ARG, "boundary-normal weights are supported by the TILED and ATOMIC paths");
     if (m->dim == 3) {
         if (prec == EM_PREC_FP64) return dispatch_what<3, EM_PREC_FP64>(m, what, A, s);
         if (prec == EM_PREC_DW) return dispatch_what<3, EM_PREC_DW>(m, what, A, s);

@@ -90,3 +90,36 @@ def test_traditional_dual_faces(name):
     assert_close_n(nt, oracle.traditional(m.dim, m.x, m.elems, oracle_topo(name)), m, "traditional n")
     rn, _, _ = oracle_fwd(name)
     assert_close_n(nt, rn, m, "traditional vs proposed n")
+
+
+@pytest.mark.parametrize("name", ["tri16", "kuhn5", "kuhn7_off", "single3"])
+def test_adjoint_boundary_weights(name):
+    """L = sum w.n + sum c V + sum bw.bnormal: the atomic and tiled adjoints
+    and the fused tiled pass against the oracle, and autograd through all
+    three outputs."""
+    from paper_2502_00778_gb300 import api
+    m, x, topo = _setup(name)
+    w, c = loss_weights(name)
+    t = oracle_topo(name)
+    rng = np.random.Generator(np.random.PCG64(17))
+    bw = rng.standard_normal((len(t.bnode), m.dim))
+    wt, ct, bt = (torch.from_numpy(a).to(DEV) for a in (w, c, bw))
+    rg = oracle.adjoint(m.dim, m.x, m.elems, t, w, c, bw)
+    g = api.edge_metrics_adjoint(topo, x, wt, ct, "fp64", "atomic", bw=bt)
+    assert_close_g(g.cpu().numpy(), rg)
+    api.plan_build(topo, 64)
+    for prec in ("fp64", "dw"):
+        g = api.edge_metrics_adjoint(topo, x, wt, ct, prec, "tiled", bw=bt)
+        assert_close_g(g.cpu().numpy(), rg)
+        _, _, _, g = api.edge_metrics_fused(topo, x, wt, ct, prec, path="tiled", bw=bt)
+        assert_close_g(g.cpu().numpy(), rg)
+    g = api.edge_metrics_adjoint(topo, x, wt, ct, "mixed", "tiled", bw=bt)
+    assert np.abs(g.cpu().numpy() - rg).max() <= 1e-5 * np.abs(rg).max()
+    xr = x.clone().requires_grad_(True)
+    n, v, b = api.EdgeMetrics.apply(xr, topo, "fp64", "atomic")
+    L = (n * wt).sum() + (v * ct).sum() + (b * bt).sum()
+    L.backward()
+    assert_close_g(xr.grad.cpu().numpy(), rg)
+    from paper_2502_00778_gb300 import EMError
+    with pytest.raises(EMError):
+        api.edge_metrics_adjoint(topo, x, wt, ct, "dw", "gather", bw=bt)
