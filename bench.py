@@ -136,15 +136,18 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    the summary was taken on the current source of that kernel."""
+def kernel_traffic(kernel, tile=None):
+    """DRAM bytes per launch of `kernel` (at tile size `tile`) from the
+    committed ncu summary, if the summary was taken on the current source of
+    that kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         j = json.load(open(p))
-        ent = j.get(kernel)
+        ent = j.get(f"{kernel}|tile{tile}") or j.get(kernel)
+        if ent and tile is not None and ent.get("tile_nodes") not in (None, tile):
+            return None
         if not ent:
             return None
         src = os.path.join(ROOT, ent["source"])
@@ -391,7 +394,7 @@ def run_ours(args):
     ab = algorithmic_bytes(m, topo, what, path)
     peak, peak_kind = peaks()
     achieved = ab / (kern_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(kname)
+    traffic = kernel_traffic(kname, tile)
     step_bytes = algorithmic_bytes(m, topo, "fused", path)
 
     # ---- end to end through the public API with host buffers ----
