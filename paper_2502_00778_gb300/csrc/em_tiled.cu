@@ -1008,58 +1008,52 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]]));
                 const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
                 V h = F::sgn(F::mul(Cs, f24), s);
-                // g_i is needed for owned node i, and all three for node 0
-                V g1[3], g2[3], g3[3];
-                if (o0 || o1) {
+                // g_k = -s/12 (A_{k+1} x X_{k+2} - A_{k+2} x X_{k+1}) + h N_k for
+                // k = 1, 2, 3 (indices cyclic, X = (a, b, c)): one loop body with
+                // the operand vectors rotated by one position per iteration; g_k
+                // is needed for owned node k, and all three for node 0
+                V Ar[3][3], Xr[3][3], Nr[3][3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    Ar[0][d] = A1[d]; Ar[1][d] = A2[d]; Ar[2][d] = A3[d];
+                    Xr[0][d] = a[d]; Xr[1][d] = b[d]; Xr[2][d] = c[d];
+                    Nr[0][d] = N1[d]; Nr[1][d] = N2[d]; Nr[2][d] = N3[d];
+                }
+                int vr0 = cn.v[1], vr1 = cn.v[2], vr2 = cn.v[3];
+                V gs[3] = {F::cst(0.0), F::cst(0.0), F::cst(0.0)};
+#pragma unroll 1
+                for (int k = 0; k < 3; k++) {
+                    const bool own = vr0 < ti.n_own;
+                    if (o0 || own) {
+                        V gk[3];
+#pragma unroll
+                        for (int d = 0; d < 3; d++) {
+                            const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+                            V g = F::sub(F::det2(Ar[1][d1], Xr[2][d2], Ar[1][d2], Xr[2][d1]),
+                                         F::det2(Ar[2][d1], Xr[1][d2], Ar[2][d2], Xr[1][d1]));
+                            gk[d] = F::add(F::sgn(F::mul(g, f12), s), F::mul(h, Nr[0][d]));
+                        }
+                        if (own) {
+#pragma unroll
+                            for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, vr0 * 3 + d, FX::q(gk[d], sg_g));
+                        }
+                        if (o0) {
+#pragma unroll
+                            for (int d = 0; d < 3; d++) gs[d] = F::add(gs[d], gk[d]);
+                        }
+                    }
+                    // rotate: position 0 takes the next k
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                        V ga = F::sub(F::det2(A2[d1], c[d2], A2[d2], c[d1]), F::det2(A3[d1], b[d2], A3[d2], b[d1]));
-                        g1[d] = F::add(F::sgn(F::mul(ga, f12), s), F::mul(h, N1[d]));
+                        V t0 = Ar[0][d]; Ar[0][d] = Ar[1][d]; Ar[1][d] = Ar[2][d]; Ar[2][d] = t0;
+                        V t1 = Xr[0][d]; Xr[0][d] = Xr[1][d]; Xr[1][d] = Xr[2][d]; Xr[2][d] = t1;
+                        V t2 = Nr[0][d]; Nr[0][d] = Nr[1][d]; Nr[1][d] = Nr[2][d]; Nr[2][d] = t2;
                     }
-                } else {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) g1[d] = F::cst(0.0);
-                }
-                if (o0 || o2) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                        V gb = F::sub(F::det2(A3[d1], a[d2], A3[d2], a[d1]), F::det2(A1[d1], c[d2], A1[d2], c[d1]));
-                        g2[d] = F::add(F::sgn(F::mul(gb, f12), s), F::mul(h, N2[d]));
-                    }
-                } else {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) g2[d] = F::cst(0.0);
-                }
-                if (o0 || o3) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                        V gc = F::sub(F::det2(A1[d1], b[d2], A1[d2], b[d1]), F::det2(A2[d1], a[d2], A2[d2], a[d1]));
-                        g3[d] = F::add(F::sgn(F::mul(gc, f12), s), F::mul(h, N3[d]));
-                    }
-                } else {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) g3[d] = F::cst(0.0);
-                }
-                if (o1) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[1] * 3 + d, FX::q(g1[d], sg_g));
-                }
-                if (o2) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[2] * 3 + d, FX::q(g2[d], sg_g));
-                }
-                if (o3) {
-#pragma unroll
-                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[3] * 3 + d, FX::q(g3[d], sg_g));
+                    const int tv = vr0; vr0 = vr1; vr1 = vr2; vr2 = tv;
                 }
                 if (o0) {
 #pragma unroll
-                    for (int d = 0; d < 3; d++)
-                        acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d,
-                                    FX::q(F::sgn(F::add(F::add(g1[d], g2[d]), g3[d]), -1.f), sg_g));
+                    for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d, FX::q(F::sgn(gs[d], -1.f), sg_g));
                 }
             }
         } else {
