@@ -129,3 +129,28 @@ def test_adjoint_96_fd():
     nodes = meshgen.generate.fd_nodes(m.n_nodes, 1000, seed=SEED + 6)
     gfd = oracle.fd_gradient(3, m.x, m.elems, t, w, c, nodes, 1e-6 * m.h)
     assert np.abs(g[nodes] - gfd).max() <= 1e-7 * np.abs(rg).max()
+
+
+def test_paper_2d_grid_size():
+    """The paper's 2D grid size (255^2 x 2 = 130,050 triangles, 65,536 nodes):
+    the tiled fused DW step and the CSR path against the full oracle."""
+    from paper_2502_00778_gb300 import api
+    m = _mesh("tri255")
+    assert (m.n_nodes, m.n_elems) == (65536, 130050)
+    x = torch.from_numpy(m.x).to(DEV)
+    topo = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+    t = oracle.topology(2, m.elems, m.x)
+    assert np.array_equal(topo.edges.cpu().numpy(), t.edges)
+    rn, rv, rb = oracle.direct(2, m.x, m.elems, t)
+    w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, 2, seed=SEED + 9)
+    rg = oracle.adjoint(2, m.x, m.elems, t, w, c)
+    api.plan_build(topo, 128)
+    n, v, b, g = api.edge_metrics_fused(topo, x, torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV), "dw",
+                                        path="tiled")
+    h = m.h
+    assert np.abs(n.cpu().numpy() - rn).max() <= 1e-12 * h
+    assert np.abs(v.cpu().numpy() - rv).max() <= 1e-12 * h * h
+    assert np.abs(b.cpu().numpy() - rb).max() <= 1e-12 * h
+    assert np.abs(g.cpu().numpy() - rg).max() <= 1e-12 * np.abs(rg).max()
+    n2, v2, b2 = api.edge_metrics(topo, x, "fp64", "csr")
+    assert np.array_equal(n2.cpu().numpy(), rn) and np.array_equal(v2.cpu().numpy(), rv)
