@@ -1,15 +1,23 @@
-// EM_PATH_GATHER: tiled, deterministic gather of the grid metrics and their
-// adjoint (plan layout in em_plan.cuh).
+// The tiled paths (plan layout in em_plan.cuh).  One CTA per tile; a tile
+// owns a range of nodes, the edges whose lower end it owns and its boundary
+// nodes, and computes every element that touches an owned node.  The tile's
+// node coordinates (and, for the adjoint, w and c) are staged in shared
+// memory (relative to the tile's first node for the FP32-based forms).  Two
+// ways of summing the element contributions into the owned outputs:
 //
-// One CTA per tile.  The tile's node coordinates are staged in shared memory
-// (relative to the tile's first node for the FP32-based forms).  Elements are
-// processed in chunks of one element per thread: each thread computes the
-// element's three needed face area vectors and its volume (and, for the
-// adjoint, the gradient of the element's share of L) and stages them in shared
-// memory; then every owned edge / node / boundary node sums its own slots of
-// the chunk in the fixed order of the plan's gather lists.  Each output is
-// produced by exactly one thread of one CTA and written once: no atomics, and
-// the result is bit-identical from run to run.
+// EM_PATH_GATHER (run_tile): elements are processed in chunks of one element
+// per thread; each thread stages its element's three needed face area
+// vectors, its volume (and, for the adjoint, its gradient terms) in shared
+// memory, then every owned edge / node / boundary node sums its own slots of
+// the chunk in the fixed order of the plan's gather lists.
+//
+// EM_PATH_TILED (run_tile_scatter): each element adds its contributions to
+// the owned targets directly, with shared-memory integer atomics on exact
+// fixed-point limbs (see the scatter section below); elements are grouped by
+// which of their nodes the tile owns, so warps skip unowned outputs together.
+//
+// Either way each output is produced by one CTA and written once, with no
+// global atomics, and the result is bit-identical from run to run.
 //
 // Element formulas (local nodes in ascending global id, so the lower end of
 // edge (p,q), p<q, is local node p), 3D: a,b,c = x1-x0, x2-x0, x3-x0,
