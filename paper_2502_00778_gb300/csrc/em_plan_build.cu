@@ -400,8 +400,13 @@ __global__ void k_tile_slot_max(int64_t n_tiles, const TileInfo* tiles, const in
     }
 }
 
+// largest run length ptr[i+1] - ptr[i]: a warp reduction, then one atomic
+// per warp (one atomic per element on a single address would serialise)
 __global__ void k_max_run(const int32_t* ptr, int64_t n, int64_t* maxv) {
-    GRID_LOOP(i, n) atomicMax((unsigned long long*)maxv, (unsigned long long)(ptr[i + 1] - ptr[i]));
+    unsigned m = 0u;
+    GRID_LOOP(i, n) m = max(m, (unsigned)(ptr[i + 1] - ptr[i]));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)maxv, (unsigned long long)m);
 }
 
 __global__ void k_key_counts(const uint64_t* k, int64_t n, int32_t* cnt) {
