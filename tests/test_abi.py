@@ -70,3 +70,31 @@ def test_workspace_queries_need_no_device(lib):
     st = L.em_edge_build(3, 1000, 5000, None, None, None, ctypes.byref(sz), None, 0, None, None, None, None, None, 0,
                          None, 0, cnt, None)
     assert st == 0 and sz.value > 5000 * 6 * 24
+
+
+def test_newer_entry_points_reject_bad_arguments(lib):
+    """Argument errors of the residual, traditional, adjoint-with-weights and
+    batched entry points come back as EM_ERR_ARG with a message, before any
+    device work."""
+    import paper_2502_00778_gb300 as p
+    L = p.load()
+    buf = ctypes.create_string_buffer(256)
+    sz = ctypes.c_size_t(0)
+    assert L.em_edge_residual(None, None, None, None, None, None, ctypes.byref(sz), None) == -1
+    L.em_last_error(buf, 256)
+    assert b"mesh" in buf.value
+    assert L.em_edge_areas_traditional(None, None, None, None) == -1
+    m = p._lib.EmMesh()
+    m.dim, m.n_nodes, m.n_elems, m.n_edges = 3, 4, 1, 6
+    m.elems = m.elem2edge = m.edges = 4096   # never dereferenced: validation fails first
+    assert L.em_edge_areas_traditional(ctypes.byref(m), None, None, None) == -1   # x and n_edge NULL
+    m.plan = 4096
+    fake = ctypes.c_void_p(4096)
+    st = L.em_edge_metrics_adjoint(ctypes.byref(m), 1, 1, fake, fake, fake, fake, fake, None, ctypes.byref(sz), None)
+    assert st == -1
+    L.em_last_error(buf, 256)
+    assert b"boundary-normal" in buf.value      # weights are refused on the ordered-gather path
+    big = ctypes.c_size_t(1 << 20)
+    info = (ctypes.c_int64 * 16)()
+    st = L.em_batched_fwd_adj(0, None, None, info, 3, 1, 0, None, fake, ctypes.byref(big), None)
+    assert st == -1
