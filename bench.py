@@ -222,10 +222,11 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def batched_forms(api, dev, stream, n_meshes=64):
     """The batched configuration: 64 Kuhn grids, n ~ U{8..64} cells per side,
-    jitter ~ U[0.1, 0.3] h.  Forward + adjoint of all of them in ONE persistent
-    launch replayed from a captured CUDA graph, per arithmetic form, against
-    the plain FP64 path (atomic scatter, two launches per grid) and per-grid
-    launches of the fused tiled kernel."""
+    jitter ~ U[0.1, 0.3] h.  Forward + adjoint of all of them in ONE launch
+    replayed from a captured CUDA graph, per arithmetic form (tile size and
+    launch shape, one CTA per work item or persistent CTAs, chosen by the
+    autotuner), against the plain FP64 path (atomic scatter, two launches per
+    grid) and per-grid launches of the fused tiled kernel."""
     import torch
     ms = meshgen.generate.cached_batched_set(n_meshes, cache_dir=os.environ.get("EM_MESH_CACHE") or
                                              os.path.join(ROOT, "_build", "meshcache"))
@@ -233,7 +234,6 @@ def batched_forms(api, dev, stream, n_meshes=64):
     for k, mm in enumerate(ms):
         x = torch.from_numpy(mm.x).to(dev)
         t = api.edge_build(torch.from_numpy(mm.elems).to(dev), x)
-        api.plan_build(t, 96)
         w, c = meshgen.generate.loss_weights(t.n_edges, mm.n_nodes, 3, seed=meshgen.SEED_BASE + 100 + k)
         topos.append(t)
         xs.append(x)
@@ -261,17 +261,22 @@ def batched_forms(api, dev, stream, n_meshes=64):
            "cells_per_side": [int(round((mm.n_elems / 6) ** (1 / 3))) for mm in ms]}
     base = timed(plain_fp64)
     out["plain_fp64_per_grid_ms"] = round(base, 4)
+    from paper_2502_00778_gb300 import autotune
     for prec in ("dw", "mixed", "fp64"):
         def per_grid():
             for t, x, w, c in zip(topos, xs, wsl, cs):
                 api.edge_metrics_fused(t, x, w, c, prec, path="tiled")
-        bt = api.Batch(topos, xs, wsl, cs, prec)
+        # tile size and launch shape (item grid / persistent) by the autotuner
+        tile, blocks, sweep = autotune.tune_batch(topos, xs, wsl, cs, prec)
+        bt = api.Batch(topos, xs, wsl, cs, prec, blocks=blocks)
         g = bt.capture()
         ms_b = timed(g.replay)
         bt.check_status()
         ms_p = timed(per_grid)
         out[prec] = {"graph_ms": round(ms_b, 4), "elements_per_s": n_el / (ms_b * 1e-3),
-                     "speedup_vs_plain_fp64": base / ms_b, "per_grid_tiled_ms": round(ms_p, 4)}
+                     "speedup_vs_plain_fp64": base / ms_b, "per_grid_tiled_ms": round(ms_p, 4),
+                     "tile_nodes": tile, "launch": "item grid" if blocks == 0 else "persistent",
+                     "sweep_ms": sweep}
     return out
 
 
@@ -482,17 +487,18 @@ def run_ours(args):
         if have_gather:
             cand += [("fwd:tiled", q_) for q_ in ("fp64", "dw", "mixed")]
         fwd_bytes = algorithmic_bytes(m, topo, "fwd", path)
-        fwd_tile = None
         for pth, pr in cand:
             try:
-                if pth == "fwd:tiled" and fwd_tile is None:
-                    # the forward alone needs less shared memory per tile:
-                    # tune its tile size separately
+                if pth in ("gather", "tiled", "fwd:tiled"):
+                    # every tiled form runs at its own autotuned tile size
+                    # (the forward alone needs less shared memory per tile)
                     from paper_2502_00778_gb300 import autotune
-                    _, fwd_tile, fsweep = autotune.tune(topo, x, what="fwd", precision="dw",
-                                                        candidates=(96, 128, 192, 256), paths=("tiled",),
-                                                        use_cache=False)
-                    forms["fwd:tiled tile_nodes"] = {"tile_nodes": fwd_tile, "sweep_ms": fsweep}
+                    fw = pth == "fwd:tiled"
+                    _, ftile, fsweep = autotune.tune(topo, x, w, c, what="fwd" if fw else "fused", precision=pr,
+                                                     candidates=(96, 128, 160, 192, 224, 256) if fw else
+                                                     autotune.CANDIDATES, paths=("tiled",) if fw else (pth,),
+                                                     use_cache=False)
+                    forms[f"{pth}/{pr} tile_nodes"] = {"tile_nodes": ftile, "sweep_ms": fsweep}
                 def fstep():
                     if pth.startswith("traditional:"):
                         api.edge_areas_traditional(topo, x, out=outs[0])

@@ -362,27 +362,36 @@ typedef struct em_batch_item {
     double* n_edge; double* vol; double* bnormal; double* grad_x;
 } em_batch_item;
 
+/* Launch shapes of em_batched_fwd_adj (`blocks`). */
+#define EM_BATCH_ITEM_GRID   0    /* one CTA per work item (the default, fastest) */
+#define EM_BATCH_PERSISTENT (-1)  /* persistent: SMs x resident CTAs per SM */
+
 /* em_batched_fwd_adj -- forward + adjoint (as em_edge_metrics_fused) for
- * n_meshes grids of uneven size in ONE persistent launch.  The tiles of all
- * grids form one work list; resident blocks claim tiles through an atomic
- * counter and run each tile exactly as the single-grid EM_PATH_TILED pass
- * does (exact fixed-point accumulation), so every output equals
- * em_edge_metrics_fused(..., EM_PATH_TILED) bit for bit.  No block waits on
+ * n_meshes grids of uneven size in ONE launch.  The tiles of all grids form
+ * one work list of (grid, tile) items; every item runs exactly as the
+ * single-grid EM_PATH_TILED pass runs that tile (exact fixed-point
+ * accumulation), so every output equals em_edge_metrics_fused(...,
+ * EM_PATH_TILED) bit for bit, whatever the launch shape.  No block waits on
  * another block.  Grids with an edge valence above 1000 or a node valence
  * above 250 are refused (EM_ERR_ARG), as in the tiled path.
  *   items        DEVICE array [n_meshes] of em_batch_item (pointers inside
  *                are device pointers); all grids must have the same dim.
  *   tile_prefix  DEVICE int64 [n_meshes+1]: exclusive prefix sum of the grids'
  *                tile counts (plan_info[EM_PLAN_INFO_TILES]).
+ *   n_items      HOST: the number of work items, tile_prefix[n_meshes]
+ *                (1 <= n_items < 2^31); it sizes the item grid.
  *   max_info     HOST int64 [EM_PLAN_INFO_LEN]: element-wise maximum of the
  *                grids' plan_info (sizes the shared memory of the launch).
  *   dim          dimension of every grid (2 or 3).
- *   blocks       persistent grid size (0: SMs x resident blocks per SM).
+ *   blocks       EM_BATCH_ITEM_GRID (0): n_items CTAs, one per item, issued
+ *                by the hardware in item order; > 0: that many persistent
+ *                CTAs claiming items through an atomic counter;
+ *                EM_BATCH_PERSISTENT (-1): persistent, SMs x resident CTAs.
  *   status       DEVICE int32[1], written: EM_OK, or EM_ERR_ARG if an item's
  *                dim differs from `dim`.
  * Workspace: a small counter (size query with ws == NULL).  The call reads
  * nothing back to the host and allocates nothing. */
-int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix,
+int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int64_t n_items,
                        const int64_t* max_info, int dim, int precision, int blocks, int32_t* status,
                        void* ws, size_t* ws_bytes, void* stream);
 

@@ -62,7 +62,8 @@ SIGNATURES = {
     "em_edge_areas_traditional": ([_c.POINTER(EmMesh), _vp, _vp, _vp], _c.c_int),
     "em_edge_residual": ([_c.POINTER(EmMesh), _vp, _vp, _vp, _vp, _vp, _szp, _vp], _c.c_int),
     "em_check_elements": ([_c.c_int, _i64, _i64, _vp, _vp, _vp, _szp, _i64p, _vp], _c.c_int),
-    "em_batched_fwd_adj": ([_c.c_int, _vp, _vp, _i64p, _c.c_int, _c.c_int, _c.c_int, _vp, _vp, _szp, _vp], _c.c_int),
+    "em_batched_fwd_adj": ([_c.c_int, _vp, _vp, _i64, _i64p, _c.c_int, _c.c_int, _c.c_int, _vp, _vp, _szp, _vp],
+                           _c.c_int),
     "em_plan_tiles": ([_vp, _i64p, _vp], _c.c_int),
 }
 

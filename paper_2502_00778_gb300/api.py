@@ -341,12 +341,14 @@ class EdgeMetrics(torch.autograd.Function):
 
 
 class Batch:
-    """Forward + adjoint of many grids of uneven size in one persistent launch.
+    """Forward + adjoint of many grids of uneven size in one launch.
 
     All device-side descriptions (the em_batch_item array, the tile prefix
     sums, the outputs) are built once here and keep fixed addresses, so
     run() only enqueues the library call and a captured CUDA graph of run()
     can be replayed after the inputs (x, w, c) are updated in place.
+    blocks: 0 one CTA per (grid, tile) item; > 0 that many persistent CTAs
+    claiming items from a counter; -1 persistent, SMs x resident CTAs.
     """
 
     def __init__(self, topos, xs, ws, cs, precision: str = "dw", blocks: int = 0):
@@ -390,17 +392,17 @@ class Batch:
                 self.max_info[k] = max(self.max_info[k], v)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         wsb = ctypes.c_size_t(0)
-        check(L.em_batched_fwd_adj(len(topos), None, None, self.max_info, self.dim, PREC[precision], blocks, None,
-                                   None, ctypes.byref(wsb), _stream()))
+        check(L.em_batched_fwd_adj(len(topos), None, None, self.n_tiles, self.max_info, self.dim, PREC[precision],
+                                   blocks, None, None, ctypes.byref(wsb), _stream()))
         self.wsb = wsb.value
         self.wsbuf = torch.empty(max(self.wsb, 256), dtype=torch.uint8, device=dev)
 
     def run(self):
         """Enqueue the batched launch on the current stream."""
         wsb = ctypes.c_size_t(self.wsbuf.numel())
-        check(load().em_batched_fwd_adj(len(self.topos), _ptr(self.items), _ptr(self.prefix), self.max_info, self.dim,
-                                        PREC[self.precision], self.blocks, _ptr(self.status), _ptr(self.wsbuf),
-                                        ctypes.byref(wsb), _stream()))
+        check(load().em_batched_fwd_adj(len(self.topos), _ptr(self.items), _ptr(self.prefix), self.n_tiles,
+                                        self.max_info, self.dim, PREC[self.precision], self.blocks, _ptr(self.status),
+                                        _ptr(self.wsbuf), ctypes.byref(wsb), _stream()))
 
     def capture(self):
         """A CUDA graph of run(); replay() it after updating the inputs in place."""

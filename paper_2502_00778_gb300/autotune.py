@@ -1,11 +1,13 @@
-"""Tile-size autotuner for the tiled gather path.
+"""Tile-size and launch-shape autotuner for the tiled paths.
 
 The tile size (nodes per tile) sets the partition of the grid: larger tiles
 recompute fewer halo elements but need more shared memory per block, so fewer
-blocks are resident per SM.  `tune()` builds a plan for each candidate size,
-times the requested pass with CUDA events and keeps the fastest; results are
-cached in a JSON file keyed by the grid, the pass, the arithmetic form and the
-GPU, so later runs reuse the choice.
+blocks are resident per SM (the launch then switches to 512-thread CTAs).
+`tune()` builds a plan for each candidate size, times the requested pass with
+CUDA events and keeps the fastest; results are cached in a JSON file keyed by
+the grid, the pass, the arithmetic form and the GPU, so later runs reuse the
+choice.  `tune_batch()` does the same for a batch of grids, over tile sizes
+and the batched launch shapes.
 """
 from __future__ import annotations
 
@@ -100,4 +102,37 @@ def tune(topo, x, w=None, c=None, what="fused", precision="dw", candidates=CANDI
     cache[key] = {"path": best[0], "tile_nodes": best[1], "ms": best[2], "sweep": sweep}
     if use_cache:
         _store(cache)
+    return best[0], best[1], sweep
+
+
+def tune_batch(topos, xs, ws, cs, precision="dw", candidates=(96, 192, 256), shapes=(0, -1), reps=5):
+    """Pick (tile_nodes, launch shape) for the batched forward + adjoint of
+    the grids `topos`: every grid is re-planned at each candidate tile size
+    and each launch shape of api.Batch (0: one CTA per work item, -1:
+    persistent) is timed as a CUDA-graph replay.  Leaves every grid planned
+    at the winning size and returns (tile_nodes, blocks, {"tile/shape": ms})."""
+    sweep = {}
+    best = None
+    for t in candidates:
+        try:
+            for topo in topos:
+                api.plan_build(topo, t)
+        except EMError as ex:
+            sweep[f"{t}/*"] = f"unusable: {str(ex)[:80]}"
+            continue
+        for b in shapes:
+            try:
+                bt = api.Batch(topos, xs, ws, cs, precision, blocks=b)
+                g = bt.capture()
+                ms = _time(g.replay, reps)
+                bt.check_status()
+                sweep[f"{t}/{b}"] = round(ms, 4)
+                if best is None or ms < best[2]:
+                    best = (t, b, ms)
+            except EMError as ex:
+                sweep[f"{t}/{b}"] = f"unusable: {str(ex)[:80]}"
+    if best is None:
+        raise EMError(-1, f"no usable tile size among {candidates}")
+    for topo in topos:
+        api.plan_build(topo, best[0])
     return best[0], best[1], sweep

@@ -248,11 +248,11 @@ int em_plan_tiles(const void* plan, int64_t* n_tiles, void* stream) {
     return st == EM_OK ? ok() : st;
 }
 
-int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, const int64_t* max_info,
-                       int dim, int precision, int blocks, int32_t* status, void* ws, size_t* ws_bytes,
-                       void* stream) {
-    int st = batched_impl(n_meshes, items, tile_prefix, max_info, dim, precision, blocks, status, ws, ws_bytes,
-                          as_stream(stream));
+int em_batched_fwd_adj(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int64_t n_items,
+                       const int64_t* max_info, int dim, int precision, int blocks, int32_t* status, void* ws,
+                       size_t* ws_bytes, void* stream) {
+    int st = batched_impl(n_meshes, items, tile_prefix, n_items, max_info, dim, precision, blocks, status, ws,
+                          ws_bytes, as_stream(stream));
     return st == EM_OK ? ok() : st;
 }
 

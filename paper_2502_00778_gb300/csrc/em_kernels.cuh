@@ -54,7 +54,8 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
                     int64_t* plan_info, cudaStream_t s);
 int plan_tiles_impl(const void* plan, int64_t* n_tiles, cudaStream_t s);
 
-int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, const int64_t* max_info,
-                 int dim, int precision, int blocks, int32_t* status, void* ws, size_t* ws_bytes, cudaStream_t s);
+int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int64_t n_items,
+                 const int64_t* max_info, int dim, int precision, int blocks, int32_t* status, void* ws,
+                 size_t* ws_bytes, cudaStream_t s);
 
 }  // namespace em

@@ -179,6 +179,7 @@ struct TileArgs {
     int val_e, val_v;          // largest edge / node valence of the grid
     int64_t tile_base;      // first tile handled by blockIdx.x == 0
     BwAux bwa;              // boundary-normal weights of the adjoint (bwa.bw NULL: none)
+    int ahead;              // > 0: each tile prefetches tile t + ahead's inputs into L2
 };
 
 template <int DIM, int PREC, int WHAT>
@@ -700,15 +701,87 @@ struct Fix<EM_PREC_MIXED> {
     }
 };
 
-// key of an upper bound on |a - b| for two staged coordinates
-__device__ __forceinline__ unsigned emag(double a, double b) { return mkey(a - b); }
-__device__ __forceinline__ unsigned emag(dw a, dw b) {
-    return mkey(f_to_double((fabsf(__fsub_rn(a.h, b.h)) + fabsf(a.l) + fabsf(b.l)) * 1.000001f));
-}
-
 __device__ __forceinline__ void block_max(unsigned* slot, unsigned v) {
     v = __reduce_max_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0) atomicMax(slot, v);
+}
+
+// ---- L2 prefetch of a later tile's inputs -----------------------------------
+// Tiles are dispatched in index order, so while tile t computes, tile
+// t + (resident CTAs) is about to start on some SM.  Used when one CTA fills an
+// SM (no second CTA computes while the first stages).  One warp of tile t asks
+// L2 for that tile's contiguous records (bulk prefetches of whole 16-byte
+// blocks inside each range) and for the halo coordinates and weights it will
+// gather, so its staging and element-record loads hit L2 instead of DRAM.
+// Prefetches are hints: they move no data into the program's view and raise
+// no errors for the valid addresses used here.
+__device__ __forceinline__ void l2_prefetch_range(const void* p, long long bytes) {
+    if (bytes <= 0) return;
+    const unsigned long long b = (unsigned long long)__cvta_generic_to_global(p);
+    unsigned long long a = (b + 15) & ~15ull;
+    const unsigned long long e = (b + (unsigned long long)bytes) & ~15ull;
+    while (a < e) {
+        const unsigned n = (unsigned)(e - a < 65536ull ? e - a : 65536ull);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+        a += n;
+    }
+}
+
+__device__ __forceinline__ void l2_prefetch_line(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((unsigned long long)__cvta_generic_to_global(p)));
+}
+
+template <int DIM, bool ADJ>
+__device__ void prefetch_tile_l2(const TileArgs& A, int t2, int lane) {
+    if (t2 >= A.n_tiles) return;
+    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
+    const TileInfo ti = plan_at<TileInfo>(A.plan, H->off_tiles)[t2];
+    const int32_t* halo = plan_at<int32_t>(A.plan, H->off_halo) + ti.halo_off;
+    const int32_t* hedge = plan_at<int32_t>(A.plan, H->off_hedge) + ti.hedge_off;
+    // contiguous ranges, one lane each
+    switch (lane) {
+        case 0: l2_prefetch_range(plan_at<ElemConn>(A.plan, H->off_conn) + ti.elem_off, (long long)sizeof(ElemConn) * ti.n_el); break;
+        case 1:
+            if (ADJ) l2_prefetch_range(plan_at<ElemEdges>(A.plan, H->off_tedge) + ti.elem_off, (long long)sizeof(ElemEdges) * ti.n_el);
+            break;
+        case 2: l2_prefetch_range(A.x + int64_t(ti.node0) * DIM, 8ll * DIM * ti.n_own); break;
+        case 3:
+            if (ADJ) l2_prefetch_range(A.w + int64_t(ti.edge0) * DIM, 8ll * DIM * ti.n_eo);
+            break;
+        case 4: l2_prefetch_range(halo, 4ll * ti.n_halo); break;
+        case 5:
+            if (ADJ) l2_prefetch_range(hedge, 4ll * ti.n_hedge);
+            break;
+        case 6:
+            if (ADJ && A.c) l2_prefetch_range(A.c + ti.node0, 8ll * ti.n_own);
+            break;
+        case 7: l2_prefetch_range(plan_at<TileBFace>(A.plan, H->off_tbf) + ti.bf_off, (long long)sizeof(TileBFace) * ti.n_bf); break;
+        case 8: l2_prefetch_range(A.bnode + ti.bnode0, 4ll * ti.n_bo); break;
+        default: break;
+    }
+    // gathered rows: the index loads are issued 8 per lane before their prefetches
+    constexpr int PB = 8;
+    for (int i0 = lane; i0 < ti.n_halo; i0 += PB * 32) {
+        int v[PB];
+#pragma unroll
+        for (int u = 0; u < PB; u++) v[u] = i0 + u * 32 < ti.n_halo ? halo[i0 + u * 32] : -1;
+#pragma unroll
+        for (int u = 0; u < PB; u++) {
+            if (v[u] < 0) continue;
+            l2_prefetch_line(A.x + int64_t(v[u]) * DIM);
+            if (ADJ && A.c) l2_prefetch_line(A.c + v[u]);
+        }
+    }
+    if (ADJ) {
+        for (int i0 = lane; i0 < ti.n_hedge; i0 += PB * 32) {
+            int e[PB];
+#pragma unroll
+            for (int u = 0; u < PB; u++) e[u] = i0 + u * 32 < ti.n_hedge ? hedge[i0 + u * 32] : -1;
+#pragma unroll
+            for (int u = 0; u < PB; u++)
+                if (e[u] >= 0) l2_prefetch_line(A.w + int64_t(e[u]) * DIM);
+        }
+    }
 }
 
 struct SmemS {
@@ -735,8 +808,10 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     return s;
 }
 
-template <int DIM, int PREC, int WHAT>
-__device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char* smem) {
+// pf(lane) is called by the last warp once the tile's staging is done: it may
+// prefetch a later tile's inputs into L2 while the other warps compute
+template <int DIM, int PREC, int WHAT, int NTH, class PF>
+__device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char* smem, const PF& pf) {
     using F = Form<PREC>;
     using FX = Fix<PREC>;
     using C = typename F::C;
@@ -768,13 +843,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     // ---- clear accumulators --------------------------------------------------
     if (tid < 16) red[tid] = 0u;
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < NL * se; q += NT) acc_e[q] = 0;
-        for (int q = tid; q < NL * sv; q += NT) acc_v[q] = 0;
-        for (int q = tid; q < NL * sb; q += NT) acc_b[q] = 0;
+        for (int q = tid; q < NL * se; q += NTH) acc_e[q] = 0;
+        for (int q = tid; q < NL * sv; q += NTH) acc_v[q] = 0;
+        for (int q = tid; q < NL * sb; q += NTH) acc_b[q] = 0;
     }
     if (WHAT & DO_ADJ)
-        for (int q = tid; q < NL * sgs; q += NT) acc_g[q] = 0;
-    for (int i = tid; i < ti.n_own; i += NT) bmap[i] = -1;
+        for (int q = tid; q < NL * sgs; q += NTH) acc_g[q] = 0;
+    for (int i = tid; i < ti.n_own; i += NTH) bmap[i] = -1;
     __syncthreads();
 
     // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
@@ -786,11 +861,11 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     constexpr int SB = 4, SBW = 8;
     unsigned wm = 0u, cm = 0u;
     float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
-    for (int i0 = tid; i0 < nnodes; i0 += SB * NT) {
+    for (int i0 = tid; i0 < nnodes; i0 += SB * NTH) {
         int64_t v[SB];
 #pragma unroll
         for (int u = 0; u < SB; u++) {
-            const int i = i0 + u * NT;
+            const int i = i0 + u * NTH;
             v[u] = i >= nnodes ? -1 : (i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]));
         }
         double xv[SB][DIM], cv[SB];
@@ -804,7 +879,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
 #pragma unroll
         for (int u = 0; u < SB; u++) {
             if (v[u] < 0) continue;
-            const int i = i0 + u * NT;
+            const int i = i0 + u * NTH;
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
                 const C xc = F::coord(xv[u][d], org[d]);
@@ -820,11 +895,11 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     }
     if (WHAT & DO_ADJ) {
         const int nte = ti.n_eo + ti.n_hedge;
-        for (int i0 = tid; i0 < nte; i0 += SBW * NT) {
+        for (int i0 = tid; i0 < nte; i0 += SBW * NTH) {
             int64_t e[SBW];
 #pragma unroll
             for (int u = 0; u < SBW; u++) {
-                const int i = i0 + u * NT;
+                const int i = i0 + u * NTH;
                 e[u] = i >= nte ? -1 : (i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]));
             }
             double wv[SBW][DIM];
@@ -836,7 +911,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
 #pragma unroll
             for (int u = 0; u < SBW; u++) {
                 if (e[u] < 0) continue;
-                const int i = i0 + u * NT;
+                const int i = i0 + u * NTH;
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const V w1 = F::from_double(wv[u][d]);
@@ -846,7 +921,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             }
         }
     }
-    for (int k = tid; k < ti.n_bo; k += NT) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
+    for (int k = tid; k < ti.n_bo; k += NTH) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
     if (WHAT & DO_ADJ) {
         block_max(red + 1, wm);
         block_max(red + 2, cm);
@@ -864,14 +939,14 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
         constexpr int EB = 8;
         unsigned lk = 0u;
         float lf = 0.f;
-        for (int i0 = tid; i0 < ti.n_el; i0 += EB * NT) {
+        for (int i0 = tid; i0 < ti.n_el; i0 += EB * NTH) {
             ElemConn cb[EB];
 #pragma unroll
             for (int u = 0; u < EB; u++)
-                if (i0 + u * NT < ti.n_el) cb[u] = conn[i0 + u * NT];
+                if (i0 + u * NTH < ti.n_el) cb[u] = conn[i0 + u * NTH];
 #pragma unroll
             for (int u = 0; u < EB; u++) {
-                if (i0 + u * NT >= ti.n_el) continue;
+                if (i0 + u * NTH >= ti.n_el) continue;
 #pragma unroll
                 for (int r = 1; r <= DIM; r++)
 #pragma unroll
@@ -918,6 +993,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     }
     __syncthreads();
     const int sg_e = sgv[0], sg_v = sgv[1], sg_b = sgv[2], sg_g = sgv[3];
+    if ((tid >> 5) == (NTH >> 5) - 1) pf(tid & 31);
 
     // ---- elements: compute and scatter to owned targets -------------------
     // warps take chunks of 32 consecutive elements from a shared counter (the
@@ -1133,7 +1209,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     }
 
     // ---- boundary faces ------------------------------------------------------
-    for (int j = tid; j < ti.n_bf; j += NT) {
+    for (int j = tid; j < ti.n_bf; j += NTH) {
         const TileBFace f = tbf[j];
         if (DIM == 3) {
             V u[3], tt[3];
@@ -1238,14 +1314,14 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
     const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < ti.n_eo * DIM; q += NT)
+        for (int q = tid; q < ti.n_eo * DIM; q += NTH)
             A.n_out[int64_t(ti.edge0) * DIM + q] = FX::out(acc_load<NL>(acc_e, se, q), sg_e, esc);
-        for (int q = tid; q < ti.n_bo * DIM; q += NT)
+        for (int q = tid; q < ti.n_bo * DIM; q += NTH)
             A.bnormal[int64_t(ti.bnode0) * DIM + q] = FX::out(acc_load<NL>(acc_b, sb, q), sg_b, bsc);
-        for (int q = tid; q < ti.n_own; q += NT) A.vol[int64_t(ti.node0) + q] = FX::out(acc_load<NL>(acc_v, sv, q), sg_v, vsc);
+        for (int q = tid; q < ti.n_own; q += NTH) A.vol[int64_t(ti.node0) + q] = FX::out(acc_load<NL>(acc_v, sv, q), sg_v, vsc);
     }
     if (WHAT & DO_ADJ)
-        for (int q = tid; q < ti.n_own * DIM; q += NT)
+        for (int q = tid; q < ti.n_own * DIM; q += NTH)
             A.grad[int64_t(ti.node0) * DIM + q] = FX::out(acc_load<NL>(acc_g, sgs, q), sg_g, 1.0);
 }
 
@@ -1255,10 +1331,16 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
 template <int PREC, int WHAT>
 constexpr int scatter_min_ctas() { return (PREC == EM_PREC_MIXED || WHAT == DO_FWD) ? 3 : 2; }
 
-template <int DIM, int PREC, int WHAT>
-__global__ void __launch_bounds__(NT, scatter_min_ctas<PREC, WHAT>()) k_tile_scatter(TileArgs A) {
+// NTH = 2 NT for tiles so large that one CTA fills an SM's shared memory:
+// the register file then still holds 16 warps per SM
+template <int DIM, int PREC, int WHAT, int NTH>
+__global__ void __launch_bounds__(NTH, NTH == NT ? scatter_min_ctas<PREC, WHAT>() : 1) k_tile_scatter(TileArgs A) {
     extern __shared__ __align__(16) char smem[];
-    run_tile_scatter<DIM, PREC, WHAT>(A, (int)(A.tile_base + blockIdx.x), smem);
+    const int t = (int)(A.tile_base + blockIdx.x);
+    auto pf = [&](int lane) {
+        if (A.ahead > 0) prefetch_tile_l2<DIM, (WHAT & DO_ADJ) != 0>(A, t + A.ahead, lane);
+    };
+    run_tile_scatter<DIM, PREC, WHAT, NTH>(A, t, smem, pf);
 }
 
 template <int DIM, int PREC, int WHAT>
@@ -1273,16 +1355,42 @@ int launch_tiles_scatter(const em_mesh* m, TileArgs& A, cudaStream_t s) {
         return fail(EM_ERR_ARG, "tile needs " + std::to_string(L.total) +
                                     " bytes of shared memory (> 227 KB): rebuild the plan with a smaller tile_nodes");
     if (L.total > 48 * 1024 && L.total > configured) {
-        EM_CUDA_TRY(cudaFuncSetAttribute(k_tile_scatter<DIM, PREC, WHAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024));
+        EM_CUDA_TRY(cudaFuncSetAttribute(k_tile_scatter<DIM, PREC, WHAT, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        if constexpr (DIM == 3)
+            EM_CUDA_TRY(cudaFuncSetAttribute(k_tile_scatter<DIM, PREC, WHAT, 2 * NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         configured = 227 * 1024;
     }
+    // one resident CTA of NT threads per SM leaves half the register file
+    // idle: such tiles run with 2 NT threads (3D; the results do not depend
+    // on the thread count)
+    bool wide = false;
+    int per_sm = 0;
+    EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<DIM, PREC, WHAT, NT>, NT, L.total));
+    if constexpr (DIM == 3) {
+        if (per_sm < 2) {
+            wide = true;
+            EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_scatter<DIM, PREC, WHAT, 2 * NT>,
+                                                                      2 * NT, L.total));
+        }
+    }
+    // with one CTA per SM nothing hides a tile's staging latency: tile t
+    // prefetches the tile that starts after it (tiles resident at once ahead)
+    A.ahead = per_sm == 1 ? num_sms() : 0;
     const int64_t n_tiles = m->plan_info[EM_PLAN_INFO_TILES];
     const int64_t chunk = 1 << 30;
     for (int64_t base = 0; base < n_tiles; base += chunk) {
         A.tile_base = base;
         int64_t nb = n_tiles - base < chunk ? n_tiles - base : chunk;
-        k_tile_scatter<DIM, PREC, WHAT><<<(unsigned)nb, NT, L.total, s>>>(A);
+        if constexpr (DIM == 3) {
+            if (wide)
+                k_tile_scatter<DIM, PREC, WHAT, 2 * NT><<<(unsigned)nb, 2 * NT, L.total, s>>>(A);
+            else
+                k_tile_scatter<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
+        } else {
+            k_tile_scatter<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
+        }
         note_launches(1);
     }
     EM_CUDA_TRY(cudaGetLastError());
@@ -1332,10 +1440,15 @@ int dispatch_what(const em_mesh* m, int what, TileArgs& A, cudaStream_t s) {
     return launch_tiles<DIM, PREC, DO_FWD | DO_ADJ>(m, A, s);
 }
 
-// ---- batched: persistent blocks drain the tiles of many grids ---------------
-// Work item = (grid, tile), numbered through the grids' tile prefix sums; each
-// block claims items from one atomic counter and runs the tiled scatter on
-// them, so the results are those of the single-grid tiled path.
+// ---- batched: the tiles of many grids in one launch --------------------------
+// Work item = (grid, tile), numbered through the grids' tile prefix sums.  Two
+// launch shapes run each item through the same tiled scatter, so both give
+// the results of the single-grid tiled path bit for bit:
+//   item grid (default): one CTA per item, dispatched by the hardware in item
+//     order;
+//   persistent: a fixed set of CTAs claims items through one atomic counter.
+// The persistent loop around the element loop leaves the register allocator
+// less room (it spills at this register budget), so the item grid is faster.
 __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs& A) {
     A.plan = it.mesh.plan;
     A.bnode = it.mesh.bnode;
@@ -1346,14 +1459,64 @@ __device__ __forceinline__ void args_from_mesh(const em_batch_item& it, TileArgs
     A.val_v = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_NODE_VALENCE];
     A.tile_base = 0;
     A.bwa = BwAux{nullptr, nullptr, nullptr};
+    A.ahead = 0;
 }
 
-template <int DIM, int PREC>
-__global__ void __launch_bounds__(NT, (scatter_min_ctas<PREC, DO_FWD | DO_ADJ>()))
+// last grid whose prefix <= wk
+__device__ __forceinline__ int item_grid(const int64_t* pre, int n_meshes, int64_t wk) {
+    int lo = 0, hi = n_meshes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= wk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int DIM>
+__device__ void prefetch_item_l2(const em_batch_item* items, const int64_t* pre, int n_meshes, int64_t nx, int lane) {
+    const int g = item_grid(pre, n_meshes, nx);
+    if (items[g].mesh.dim != DIM) return;
+    TileArgs B;
+    args_from_mesh(items[g], B);
+    prefetch_tile_l2<DIM, true>(B, (int)(nx - pre[g]), lane);
+}
+
+// one CTA per work item; `ahead` > 0: prefetch item wk + ahead into L2
+template <int DIM, int PREC, int NTH>
+__global__ void __launch_bounds__(NTH, (NTH == NT ? scatter_min_ctas<PREC, DO_FWD | DO_ADJ>() : 1))
+    k_batched_items(const em_batch_item* __restrict__ items, const int64_t* __restrict__ prefix, int n_meshes,
+                    Dims D, int32_t* status, int ahead) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ TileArgs sA;     // the item's arguments, read by every thread
+    const int64_t wk = blockIdx.x;
+    const int64_t total = prefix[n_meshes];
+    if (wk >= total) return;    // a grid larger than the item count: nothing to do
+    const int g = item_grid(prefix, n_meshes, wk);
+    const em_batch_item& it = items[g];
+    if (it.mesh.dim != DIM) {   // block-uniform
+        if (threadIdx.x == 0) atomicExch(status, EM_ERR_ARG);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        args_from_mesh(it, sA);
+        sA.D = D;
+    }
+    __syncthreads();
+    auto pf = [&](int lane) {
+        if (ahead > 0 && wk + ahead < total) prefetch_item_l2<DIM>(items, prefix, n_meshes, wk + ahead, lane);
+    };
+    run_tile_scatter<DIM, PREC, DO_FWD | DO_ADJ, NTH>(sA, (int)(wk - prefix[g]), smem, pf);
+}
+
+// persistent CTAs draining the work list; `prefetch`: prefetch the item
+// claimed next into L2
+template <int DIM, int PREC, int NTH>
+__global__ void __launch_bounds__(NTH, (NTH == NT ? scatter_min_ctas<PREC, DO_FWD | DO_ADJ>() : 1))
     k_batched(const em_batch_item* __restrict__ items, const int64_t* __restrict__ prefix, int n_meshes, Dims D,
-              unsigned long long* counter, int32_t* status) {
+              unsigned long long* counter, int32_t* status, int prefetch) {
     extern __shared__ __align__(16) char smem[];
     __shared__ long long s_next;
+    __shared__ TileArgs sA;
     // the tile prefix sums live in shared memory behind the tile's layout
     const SmemS L = smem_layout_s<DIM, PREC, DO_FWD | DO_ADJ>(D);
     int64_t* spre = reinterpret_cast<int64_t*>(smem + L.total);
@@ -1367,54 +1530,94 @@ __global__ void __launch_bounds__(NT, (scatter_min_ctas<PREC, DO_FWD | DO_ADJ>()
         if (wk >= total) break;
         // claim the following item now; its atomic completes while this tile runs
         if (threadIdx.x == 0) s_next = (long long)atomicAdd(counter, 1ull);
-        int lo = 0, hi = n_meshes - 1;           // last mesh whose prefix <= wk
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (spre[mid] <= wk) lo = mid; else hi = mid - 1;
-        }
-        const em_batch_item& it = items[lo];
+        const int g = item_grid(spre, n_meshes, wk);
+        const em_batch_item& it = items[g];
         if (it.mesh.dim != DIM) {   // block-uniform branch
             if (threadIdx.x == 0) atomicExch(status, EM_ERR_ARG);
             __syncthreads();         // orders the claim above before the next read of s_next
             continue;
         }
-        TileArgs A;
-        args_from_mesh(it, A);
-        A.D = D;
-        run_tile_scatter<DIM, PREC, DO_FWD | DO_ADJ>(A, (int)(wk - prefix[lo]), smem);
+        if (threadIdx.x == 0) {
+            args_from_mesh(it, sA);
+            sA.D = D;
+        }
+        __syncthreads();
+        // s_next (written before the tile's first barrier) is this block's
+        // next item
+        auto pf = [&](int lane) {
+            const long long nx = s_next;
+            if (prefetch && nx < total) prefetch_item_l2<DIM>(items, spre, n_meshes, nx, lane);
+        };
+        run_tile_scatter<DIM, PREC, DO_FWD | DO_ADJ, NTH>(sA, (int)(wk - spre[g]), smem, pf);
         __syncthreads();
     }
 }
 
-template <int DIM, int PREC>
-int launch_batched(int n_meshes, const em_batch_item* items, const int64_t* prefix, const Dims& D, int blocks,
-                   unsigned long long* counter, int32_t* status, cudaStream_t s) {
-    const SmemS L = smem_layout_s<DIM, PREC, DO_FWD | DO_ADJ>(D);
-    const size_t bytes = L.total + sizeof(int64_t) * (size_t)(n_meshes + 1);
-    if (bytes > 227 * 1024)
-        return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(bytes) +
-                                    " bytes of shared memory (> 227 KB): use a smaller tile_nodes or fewer grids");
-    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    if (blocks <= 0) {
-        int per_sm = 0;
-        EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<DIM, PREC>, NT, bytes));
-        blocks = num_sms() * (per_sm > 0 ? per_sm : 1);
+template <int DIM, int PREC, int NTH>
+int launch_batched_as(int n_meshes, const em_batch_item* items, const int64_t* prefix, int64_t n_items, const Dims& D,
+                      int blocks, int per_sm, size_t bytes, unsigned long long* counter, int32_t* status,
+                      cudaStream_t s) {
+    if (blocks == 0) {
+        // one CTA per item; with one CTA per SM, item wk prefetches the item
+        // that starts after it
+        const int ahead = per_sm == 1 ? num_sms() : 0;
+        EM_CUDA_TRY(cudaFuncSetAttribute(k_batched_items<DIM, PREC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes));
+        k_batched_items<DIM, PREC, NTH><<<(unsigned)n_items, NTH, bytes, s>>>(items, prefix, n_meshes, D, status,
+                                                                               ahead);
+    } else {
+        if (blocks < 0) blocks = num_sms() * (per_sm > 0 ? per_sm : 1);
+        EM_CUDA_TRY(cudaFuncSetAttribute(k_batched<DIM, PREC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(bytes + sizeof(int64_t) * (size_t)(n_meshes + 1))));
+        k_batched<DIM, PREC, NTH><<<blocks, NTH, bytes + sizeof(int64_t) * (size_t)(n_meshes + 1), s>>>(
+            items, prefix, n_meshes, D, counter, status, per_sm == 1 ? 1 : 0);
     }
-    k_batched<DIM, PREC><<<blocks, NT, bytes, s>>>(items, prefix, n_meshes, D, counter, status);
     note_launches(1);
     EM_CUDA_TRY(cudaGetLastError());
     return EM_OK;
 }
 
+template <int DIM, int PREC>
+int launch_batched(int n_meshes, const em_batch_item* items, const int64_t* prefix, int64_t n_items, const Dims& D,
+                   int blocks, unsigned long long* counter, int32_t* status, cudaStream_t s) {
+    const SmemS L = smem_layout_s<DIM, PREC, DO_FWD | DO_ADJ>(D);
+    const size_t bytes = L.total;
+    const size_t need = L.total + (blocks != 0 ? sizeof(int64_t) * (size_t)(n_meshes + 1) : 0);
+    if (need > 227 * 1024)
+        return fail(EM_ERR_ARG, "batched tiles need " + std::to_string(need) +
+                                    " bytes of shared memory (> 227 KB): use a smaller tile_nodes or fewer grids");
+    // as for one grid: tiles that fill an SM run with 2 NT threads (3D) and
+    // prefetch their next item (the results depend on neither)
+    int per_sm = 0;
+    EM_CUDA_TRY(cudaFuncSetAttribute(k_batched_items<DIM, PREC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)need));
+    EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_items<DIM, PREC, NT>, NT, need));
+    if constexpr (DIM == 3) {
+        if (per_sm < 2) {
+            EM_CUDA_TRY(cudaFuncSetAttribute(k_batched_items<DIM, PREC, 2 * NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+            EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_items<DIM, PREC, 2 * NT>,
+                                                                      2 * NT, need));
+            return launch_batched_as<DIM, PREC, 2 * NT>(n_meshes, items, prefix, n_items, D, blocks, per_sm, bytes,
+                                                        counter, status, s);
+        }
+    }
+    return launch_batched_as<DIM, PREC, NT>(n_meshes, items, prefix, n_items, D, blocks, per_sm, bytes, counter,
+                                            status, s);
+}
+
 }  // namespace
 
-int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, const int64_t* max_info,
-                 int dim, int precision, int blocks, int32_t* status, void* ws, size_t* ws_bytes, cudaStream_t s) {
+int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int64_t n_items,
+                 const int64_t* max_info, int dim, int precision, int blocks, int32_t* status, void* ws,
+                 size_t* ws_bytes, cudaStream_t s) {
     bool query;
     EM_TRY(check_ws(ws, ws_bytes, 256, &query));
     if (query) return EM_OK;
     if (n_meshes <= 0 || !items || !tile_prefix || !max_info || !status)
         return fail(EM_ERR_ARG, "batched call needs items, tile_prefix, max_info and status");
+    if (n_items <= 0 || n_items > 0x7fffffffLL) return fail(EM_ERR_ARG, "n_items must be in [1, 2^31)");
+    if (blocks < EM_BATCH_PERSISTENT) return fail(EM_ERR_ARG, "blocks must be >= EM_BATCH_PERSISTENT (-1)");
     if (dim != 2 && dim != 3) return fail(EM_ERR_ARG, "dim must be 2 or 3");
     if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
         return fail(EM_ERR_ARG, "batched pass supports FP64, DW and MIXED");
@@ -1436,13 +1639,13 @@ int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_p
     EM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     EM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
     if (dim == 3) {
-        if (precision == EM_PREC_FP64) return launch_batched<3, EM_PREC_FP64>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
-        if (precision == EM_PREC_DW) return launch_batched<3, EM_PREC_DW>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
-        return launch_batched<3, EM_PREC_MIXED>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+        if (precision == EM_PREC_FP64) return launch_batched<3, EM_PREC_FP64>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
+        if (precision == EM_PREC_DW) return launch_batched<3, EM_PREC_DW>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
+        return launch_batched<3, EM_PREC_MIXED>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
     }
-    if (precision == EM_PREC_FP64) return launch_batched<2, EM_PREC_FP64>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
-    if (precision == EM_PREC_DW) return launch_batched<2, EM_PREC_DW>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
-    return launch_batched<2, EM_PREC_MIXED>(n_meshes, items, tile_prefix, D, blocks, counter, status, s);
+    if (precision == EM_PREC_FP64) return launch_batched<2, EM_PREC_FP64>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
+    if (precision == EM_PREC_DW) return launch_batched<2, EM_PREC_DW>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
+    return launch_batched<2, EM_PREC_MIXED>(n_meshes, items, tile_prefix, n_items, D, blocks, counter, status, s);
 }
 
 size_t gather_ws_bytes(const em_mesh*) { return 0; }
@@ -1471,6 +1674,7 @@ int gather_run(const em_mesh* m, int prec, int what, const double* x, const doub
     A.val_e = (int)(pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_EDGE_VALENCE] : 64);
     A.val_v = (int)(pi[EM_PLAN_INFO_MAX_NODE_VALENCE] > 0 ? pi[EM_PLAN_INFO_MAX_NODE_VALENCE] : 64);
     A.tile_base = 0;
+    A.ahead = 0;
     A.bwa = bw ? *bw : BwAux{nullptr, nullptr, nullptr};
     if (A.bwa.bw && !(what & GATHER_SCATTER))
         return fail(EM_ERR_ARG, "boundary-normal weights are supported by the TILED and ATOMIC paths");

@@ -96,5 +96,13 @@ def test_newer_entry_points_reject_bad_arguments(lib):
     assert b"boundary-normal" in buf.value      # weights are refused on the ordered-gather path
     big = ctypes.c_size_t(1 << 20)
     info = (ctypes.c_int64 * 16)()
-    st = L.em_batched_fwd_adj(0, None, None, info, 3, 1, 0, None, fake, ctypes.byref(big), None)
+    st = L.em_batched_fwd_adj(0, None, None, 1, info, 3, 1, 0, None, fake, ctypes.byref(big), None)
     assert st == -1
+    st = L.em_batched_fwd_adj(1, fake, fake, 0, info, 3, 1, 0, fake, fake, ctypes.byref(big), None)
+    assert st == -1                             # no work items
+    L.em_last_error(buf, 256)
+    assert b"n_items" in buf.value
+    st = L.em_batched_fwd_adj(1, fake, fake, 1, info, 3, 1, -2, fake, fake, ctypes.byref(big), None)
+    assert st == -1                             # unknown launch shape
+    L.em_last_error(buf, 256)
+    assert b"blocks" in buf.value

@@ -33,11 +33,14 @@ def batch_inputs():
     return ms, topos, xs, ws, cs
 
 
+@pytest.mark.parametrize("blocks", [0, -1, 5])
 @pytest.mark.parametrize("prec", ["fp64", "dw", "mixed"])
-def test_batched_equals_per_grid(batch_inputs, prec):
+def test_batched_equals_per_grid(batch_inputs, prec, blocks):
+    """Item grid (0), persistent at full residency (-1) and a few persistent
+    CTAs that each drain many items (5)."""
     from paper_2502_00778_gb300 import api
     ms, topos, xs, ws, cs = batch_inputs
-    b = api.Batch(topos, xs, ws, cs, prec)
+    b = api.Batch(topos, xs, ws, cs, prec, blocks=blocks)
     b.run()
     torch.cuda.synchronize()
     b.check_status()
@@ -71,3 +74,38 @@ def test_batched_graph_replay_and_oracle(batch_inputs):
         assert np.abs(o[1].cpu().numpy() - rv).max() <= 1e-12 * m.h ** 3
         rg = oracle.adjoint(3, m.x, m.elems, ot, w.cpu().numpy(), c.cpu().numpy())
         assert np.abs(o[3].cpu().numpy() - rg).max() <= 1e-12 * np.abs(rg).max()
+
+
+@pytest.mark.parametrize("blocks", [0, -1])
+@pytest.mark.parametrize("prec", ["fp64", "dw"])
+def test_wide_tiles_equal_batched(prec, blocks):
+    """At tile_nodes 256 a tile fills an SM's shared memory: the launches run
+    512 threads per CTA and each tile prefetches a later one into L2.  The
+    batched launch (item grid or persistent, where tiles run in another
+    order and next to other grids' tiles) must still equal the per-grid pass
+    bit for bit, and the profiler (where it reports kernel names) must show
+    the 512-thread variant."""
+    from paper_2502_00778_gb300 import api
+    ms = meshgen.batched_set(3, seed=meshgen.SEED_BASE + 11, nmin=12, nmax=18)
+    topos, xs, ws, cs = [], [], [], []
+    for k, m in enumerate(ms):
+        x = torch.from_numpy(m.x).to(DEV)
+        t = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+        api.plan_build(t, 256)
+        w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, 3, seed=2000 + k)
+        topos.append(t); xs.append(x)
+        ws.append(torch.from_numpy(w).to(DEV)); cs.append(torch.from_numpy(c).to(DEV))
+    b = api.Batch(topos, xs, ws, cs, prec, blocks=blocks)
+    b.run()
+    torch.cuda.synchronize()
+    b.check_status()
+    with torch.profiler.profile(activities=[torch.profiler.ProfilerActivity.CUDA]) as prof:
+        refs = [api.edge_metrics_fused(t, x, w, c, prec, path="tiled") for t, x, w, c in zip(topos, xs, ws, cs)]
+        torch.cuda.synchronize()
+    names = {e.name for e in prof.events() if "k_tile_scatter" in e.name}
+    for o, ref in zip(b.outs, refs):
+        for a, r in zip(o, ref):
+            assert torch.equal(a, r)
+    # where the profiler reports kernel names, the wide variant is the one that ran
+    if names:
+        assert any("512" in n for n in names), names
