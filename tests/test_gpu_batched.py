@@ -1,6 +1,7 @@
-"""Batched forward + adjoint of uneven grids in one persistent launch, and
-its CUDA-graph replay: every output equals the per-grid fused tiled pass
-bit for bit (same tiles, same code, exact fixed-point sums)."""
+"""Batched forward + adjoint of uneven grids in one launch (one CTA per work
+item, or persistent CTAs draining a counter), and its CUDA-graph replay:
+every output equals the per-grid fused tiled pass bit for bit (same tiles,
+same code, exact fixed-point sums)."""
 import numpy as np
 import pytest
 

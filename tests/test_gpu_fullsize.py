@@ -1,9 +1,10 @@
 """Full-size checks in the benchmark's configuration.
 
 160^3 x 6 tets, offset 1e3 (the benchmark workload), in the benchmark's
-launch configuration (fused tiled scatter, tile_nodes 96 as the autotuner
-picks it for the fused double-word step, one launch per step; the ordered
-gather path for comparison): edge_build is checked through properties that characterise
+launch configuration (fused tiled scatter, one launch per step, at the tile
+sizes the autotuner picks there: 256 nodes for DW and FP64, which run
+512-thread CTAs with the L2 prefetch of the next tile, 128 for MIXED; the
+ordered gather path for comparison): edge_build is checked through properties that characterise
 the sorted unique edge list exactly; the metrics and the adjoint are checked
 at 2000 sampled edges and nodes, each computed by the oracle alone from the
 elements around it.  96^3 x 6 (the adjoint workload): the full gradient
@@ -37,8 +38,12 @@ def big():
     x = torch.from_numpy(m.x).to(DEV)
     el = torch.from_numpy(m.elems).to(DEV)
     topo = api.edge_build(el, x)
-    api.plan_build(topo, 96)
+    api.plan_build(topo, 256)
     return m, x, topo
+
+
+# tile_nodes per (form, path) as the benchmark's autotuner picks them
+TILE = {("dw", "tiled"): 256, ("fp64", "tiled"): 256, ("mixed", "tiled"): 128, ("dw", "gather"): 128}
 
 
 def test_edge_build_properties_160(big):
@@ -73,6 +78,7 @@ def test_sampled_parity_160(big, prec, path):
     ns = np.unique(np.concatenate([rng.choice(m.n_nodes, 1500, replace=False), rng.choice(bn, 500, replace=False)]))
     w, c = meshgen.generate.hash_weights(e, m.n_nodes, 3, SEED)
     wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
+    api.plan_build(topo, TILE[(prec, path)])
     n, v, b, g = api.edge_metrics_fused(topo, x, wt, ct, prec, path=path)
     rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], ns, SEED)
     h = m.h
@@ -123,9 +129,11 @@ def test_adjoint_96_fd():
     wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
     rg = oracle.adjoint(3, m.x, m.elems, t, w, c)
     tol = 1e-12 * np.abs(rg).max()
-    for prec, path in [("dw", "tiled"), ("fp64", "tiled"), ("dw", "gather"), ("fp64", "gather"), ("fp64", "atomic")]:
+    for prec, path, tile in [("dw", "tiled", 128), ("fp64", "tiled", 128), ("dw", "gather", 128),
+                             ("fp64", "gather", 128), ("dw", "tiled", 256), ("fp64", "atomic", 128)]:
+        api.plan_build(topo, tile)
         g = api.edge_metrics_adjoint(topo, x, wt, ct, prec, path).cpu().numpy()
-        assert np.abs(g - rg).max() <= tol, (prec, path)
+        assert np.abs(g - rg).max() <= tol, (prec, path, tile)
     nodes = meshgen.generate.fd_nodes(m.n_nodes, 1000, seed=SEED + 6)
     gfd = oracle.fd_gradient(3, m.x, m.elems, t, w, c, nodes, 1e-6 * m.h)
     assert np.abs(g[nodes] - gfd).max() <= 1e-7 * np.abs(rg).max()
