@@ -626,26 +626,18 @@ __device__ __forceinline__ double pow2d(int k) {
     return __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
 }
 
-// scale exponent such that |sum| <= bound * 2^sigma < 2^top, clamped to
-// [lo, hi] (a bound of 0 means every term is 0: any scale works)
-__device__ __forceinline__ int fx_sigma(double bound, int top, int lo, int hi) {
-    if (!(bound > 0.0)) return 0;
-    const int e = (int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1023 + 1;   // bound < 2^e
-    const int sg = top - e;
-    return sg > hi ? hi : (sg < lo ? lo : sg);
-}
+__device__ __forceinline__ int sg_clamp(int sg, int lo, int hi) { return sg > hi ? hi : (sg < lo ? lo : sg); }
 
 // Magnitudes as order-preserving 32-bit keys: the upper word of |v| as an
 // IEEE double (exponent and 20 mantissa bits).  Non-negative doubles order
-// like their bit patterns, so an integer max gives the max magnitude, and
-// key_bound() returns a double >= every value with that key.  Integer pipe
-// only, and valid over the whole double range.
+// like their bit patterns, so an integer max gives the max magnitude.  Every
+// value with key k is below the double whose upper word is k + 1, and that
+// double is below 2^key_exp(k).  Integer pipe only, and valid over the whole
+// finite double range.
 __device__ __forceinline__ unsigned mkey(double v) {
     return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
 }
-__device__ __forceinline__ double key_bound(unsigned k) {
-    return __longlong_as_double((long long)((unsigned long long)(k + 1u) << 32));
-}
+__device__ __forceinline__ int key_exp(unsigned k) { return (int)(((k + 1u) >> 20) & 0x7ffu) - 1022; }
 
 template <int PREC>
 struct Fix;
@@ -701,9 +693,18 @@ struct Fix<EM_PREC_MIXED> {
     }
 };
 
-__device__ __forceinline__ void block_max(unsigned* slot, unsigned v) {
+// block-wide maxima without a cleared slot: each warp writes its maximum to
+// its own entry of slot s (16 entries per slot), and readers take the max of
+// the entries after a barrier
+constexpr int RED_WARPS = 16;
+__device__ __forceinline__ void block_max(unsigned* wred, int s, unsigned v) {
     v = __reduce_max_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0) atomicMax(slot, v);
+    if ((threadIdx.x & 31) == 0) wred[s * RED_WARPS + (threadIdx.x >> 5)] = v;
+}
+__device__ __forceinline__ unsigned red_max(const unsigned* wred, int s, int nwarps) {
+    unsigned m = 0u;
+    for (int w = 0; w < nwarps; w++) m = max(m, wred[s * RED_WARPS + w]);
+    return m;
 }
 
 // ---- L2 prefetch of a later tile's inputs -----------------------------------
@@ -803,7 +804,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
     s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
     s.bmap = take(sizeof(int) * D.max_own);
-    s.red = take(sizeof(unsigned) * 16);
+    s.red = take(sizeof(unsigned) * (16 + 4 * RED_WARPS));
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -836,6 +837,8 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     const int se = DIM * A.D.max_eo, sv = A.D.max_own, sgs = DIM * A.D.max_own, sb = DIM * A.D.max_bo;
     int* bmap = reinterpret_cast<int*>(smem + L.bmap);
     unsigned* red = reinterpret_cast<unsigned*>(smem + L.red);
+    unsigned* wred = red + 16;
+    static_assert(NTH / 32 <= RED_WARPS, "one maximum slot per warp");
 
     const int tid = threadIdx.x;
     const int nnodes = ti.n_own + ti.n_halo;
@@ -850,7 +853,21 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     if (WHAT & DO_ADJ)
         for (int q = tid; q < NL * sgs; q += NTH) acc_g[q] = 0;
     for (int i = tid; i < ti.n_own; i += NTH) bmap[i] = -1;
-    __syncthreads();
+    // (no barrier: the cleared planes are first used after the staging and
+    // extent barriers below, and the boundary-node map is filled after them)
+
+    // 512-thread tiles (one CTA per SM, nothing hides their latency): this
+    // thread's first element records of the extent pass below are requested
+    // now, so that they arrive while the staging gathers are in flight (the
+    // 256-thread forms have no registers to spare for them)
+    constexpr int EB = 8;
+    constexpr bool HOIST = NTH > NT;
+    ElemConn ecb[HOIST ? EB : 1];
+    if constexpr (HOIST) {
+#pragma unroll
+        for (int u = 0; u < EB; u++)
+            if (tid + u * NTH < ti.n_el) ecb[u] = conn[tid + u * NTH];
+    }
 
     // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
     double org[DIM];
@@ -921,13 +938,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             }
         }
     }
-    for (int k = tid; k < ti.n_bo; k += NTH) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
     if (WHAT & DO_ADJ) {
-        block_max(red + 1, wm);
-        block_max(red + 2, cm);
+        block_max(wred, 1, wm);
+        block_max(wred, 2, cm);
     }
-    if constexpr (PREC != EM_PREC_FP64) block_max(red + 3, mkey(f_to_double(xl)));
+    if constexpr (PREC != EM_PREC_FP64) block_max(wred, 3, mkey(f_to_double(xl)));
     __syncthreads();
+    for (int k = tid; k < ti.n_bo; k += NTH) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
 
     // ---- element extent: Lx bounds every coordinate difference along an edge
     // from local node 0 of a tile element; every face vector, volume and
@@ -936,14 +953,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     // the extent of the tile.  The element records are loaded EB at a time so
     // that their loads are in flight together.
     {
-        constexpr int EB = 8;
         unsigned lk = 0u;
         float lf = 0.f;
         for (int i0 = tid; i0 < ti.n_el; i0 += EB * NTH) {
             ElemConn cb[EB];
 #pragma unroll
             for (int u = 0; u < EB; u++)
-                if (i0 + u * NTH < ti.n_el) cb[u] = conn[i0 + u * NTH];
+                if (i0 + u * NTH < ti.n_el) cb[u] = (HOIST && i0 == tid) ? ecb[HOIST ? u : 0] : conn[i0 + u * NTH];
 #pragma unroll
             for (int u = 0; u < EB; u++) {
                 if (i0 + u * NTH >= ti.n_el) continue;
@@ -959,40 +975,40 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             }
         }
         // DW / MIXED: |a - b| <= |a.h - b.h| (1 + 2^-23) + 2 max|low part|
-        block_max(red + 0, PREC == EM_PREC_FP64 ? lk : mkey(f_to_double(lf)));
+        block_max(wred, 0, PREC == EM_PREC_FP64 ? lk : mkey(f_to_double(lf)));
     }
     __syncthreads();
 
     // ---- scales: no accumulated sum can reach 2^TOP -------------------------
-    // one thread derives the scales (double arithmetic), the block reads them
-    int* sgv = reinterpret_cast<int*>(red + 4);
-    if (tid == 0) {
-        const double Lx = PREC == EM_PREC_FP64 ? key_bound(red[0])
-                                               : key_bound(red[0]) * (1.0 + 0x1p-20) + 2.0 * key_bound(red[3]);
-        const double Ke = (double)A.val_e, Kv = (double)A.val_v;
-        constexpr int T = FX::TOP, LO = FX::LO, HI = FX::HI;
-        if (DIM == 3) {
-            // |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3, |n_B| <= 8 Lx^2
-            sgv[0] = fx_sigma(32.0 * Lx * Lx * Ke, T, LO, HI);
-            sgv[1] = fx_sigma(8.0 * Lx * Lx * Lx * Kv, T, LO, HI);
-            sgv[2] = fx_sigma(32.0 * Lx * Lx * Kv, T, LO, HI);   // up to 3 boundary faces per element at a node
-            // boundary-normal weights: per face |1/2 t x K| <= 2 Lx max|bw| per component
-            const double Bm = ((WHAT & DO_ADJ) && A.bwa.bw) ? key_bound(*A.bwa.key) : 0.0;
-            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((16.0 * key_bound(red[1]) * Lx + 8.0 * key_bound(red[2]) * Lx * Lx +
-                                                 16.0 * Bm * Lx) * 2.0 * Kv, T, LO, HI)
-                                     : 0;
-        } else {
-            sgv[0] = fx_sigma(8.0 * Lx * Ke, T, LO, HI);
-            sgv[1] = fx_sigma(16.0 * Lx * Lx * Kv, T, LO, HI);
-            sgv[2] = fx_sigma(8.0 * Lx * Kv, T, LO, HI);
-            const double Bm = ((WHAT & DO_ADJ) && A.bwa.bw) ? key_bound(*A.bwa.key) : 0.0;
-            sgv[3] = (WHAT & DO_ADJ) ? fx_sigma((4.0 * key_bound(red[1]) + 4.0 * key_bound(red[2]) * Lx + 4.0 * Bm) *
-                                                2.0 * Kv, T, LO, HI)
-                                     : 0;
-        }
+    // Each bound is a product (or a sum of three products) of factors with
+    // power-of-two upper bounds, so its exponent is a sum of exponents: every
+    // thread derives the same scales with integer arithmetic, with no FP64
+    // instruction and no further barrier.  (Rounding each factor up to a power
+    // of two gives away at most a few of the 62 bits.)
+    constexpr int TP = FX::TOP, LO = FX::LO, HI = FX::HI;
+    // DW / MIXED: Lx <= b0 (1 + 2^-20) + 2 b3 < 2^(max(E0, E3) + 2), with b0 < 2^E0
+    // bounding the high-part extent (slot 0) and b3 < 2^E3 the low parts (slot 3)
+    constexpr int NW = NTH / 32;
+    const int eL = PREC == EM_PREC_FP64 ? key_exp(red_max(wred, 0, NW))
+                                        : max(key_exp(red_max(wred, 0, NW)), key_exp(red_max(wred, 3, NW))) + 2;
+    const int eKe = 32 - __clz(A.val_e > 1 ? A.val_e : 1), eKv = 32 - __clz(A.val_v > 1 ? A.val_v : 1);
+    int eg = 0;
+    if (WHAT & DO_ADJ) {
+        // |w|, |c|, |bw| < 2^Ew, 2^Ec, 2^Eb
+        const int Ew = key_exp(red_max(wred, 1, NW)), Ec = key_exp(red_max(wred, 2, NW));
+        const int Eb = A.bwa.bw ? key_exp(*A.bwa.key) : -2000;
+        if (DIM == 3)   // (16 |w| Lx + 8 |c| Lx^2 + 16 |bw| Lx) 2 Kv
+            eg = max(max(4 + Ew + eL, 3 + Ec + 2 * eL), 4 + Eb + eL) + 2 + 1 + eKv;
+        else            // (4 |w| + 4 |c| Lx + 4 |bw|) 2 Kv
+            eg = max(max(2 + Ew, 2 + Ec + eL), 2 + Eb) + 2 + 1 + eKv;
     }
-    __syncthreads();
-    const int sg_e = sgv[0], sg_v = sgv[1], sg_b = sgv[2], sg_g = sgv[3];
+    // 3D: |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3 < 8 Lx^3,
+    // |n_B| <= 8 Lx^2 with up to 3 boundary faces per element at a node;
+    // 2D: |n_i| <= 2 Lx, |det| <= 2 Lx^2, boundary edge <= 2 Lx
+    const int sg_e = sg_clamp(TP - (DIM == 3 ? 5 + 2 * eL + eKe : 3 + eL + eKe), LO, HI);
+    const int sg_v = sg_clamp(TP - (DIM == 3 ? 3 + 3 * eL + eKv : 4 + 2 * eL + eKv), LO, HI);
+    const int sg_b = sg_clamp(TP - (DIM == 3 ? 5 + 2 * eL + eKv : 3 + eL + eKv), LO, HI);
+    const int sg_g = (WHAT & DO_ADJ) ? sg_clamp(TP - eg, LO, HI) : 0;
     if ((tid >> 5) == (NTH >> 5) - 1) pf(tid & 31);
 
     // ---- elements: compute and scatter to owned targets -------------------
