@@ -110,3 +110,50 @@ def test_wide_tiles_equal_batched(prec, blocks):
     # where the profiler reports kernel names, the wide variant is the one that ran
     if names:
         assert any("512" in n for n in names), names
+
+
+def test_batched_bench_configuration():
+    """The benchmark's batched configuration: 64 Kuhn grids with n ~ U{8..64}
+    cells per side and jitter amplitude ~ U[0.1, 0.3] h (with validity
+    repair), loss weights per grid as the benchmark draws them, tile size and
+    launch shape chosen by the autotuner, one launch replayed from a captured
+    CUDA graph.  Every output equals the per-grid fused tiled pass at the same
+    tile size bit for bit, and the largest grid matches the full oracle."""
+    import os
+    from paper_2502_00778_gb300 import api, autotune
+    cache = os.environ.get("EM_MESH_CACHE") or os.path.join(os.path.dirname(os.path.dirname(__file__)), "_build",
+                                                          "meshcache")
+    ms = meshgen.generate.cached_batched_set(64, cache_dir=cache)
+    ns = [int(round((m.n_elems / 6) ** (1 / 3))) for m in ms]
+    assert min(ns) >= 8 and max(ns) <= 64
+    topos, xs, ws, cs = [], [], [], []
+    for k, m in enumerate(ms):
+        x = torch.from_numpy(m.x).to(DEV)
+        t = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+        w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, 3, seed=meshgen.SEED_BASE + 100 + k)
+        topos.append(t); xs.append(x)
+        ws.append(torch.from_numpy(w).to(DEV)); cs.append(torch.from_numpy(c).to(DEV))
+    tile, blocks, _ = autotune.tune_batch(topos, xs, ws, cs, "dw")
+    b = api.Batch(topos, xs, ws, cs, "dw", blocks=blocks)
+    g = b.capture()
+    for o in b.outs:
+        for a in o:
+            a.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    b.check_status()
+    for t, x, w, c, o in zip(topos, xs, ws, cs, b.outs):
+        ref = api.edge_metrics_fused(t, x, w, c, "dw", path="tiled")
+        for a, r in zip(o, ref):
+            assert torch.equal(a, r)
+    k = int(np.argmax([m.n_elems for m in ms]))
+    m = ms[k]
+    ot = oracle.topology(3, m.elems, m.x)
+    assert np.array_equal(topos[k].edges.cpu().numpy(), ot.edges)
+    rn, rv, rb = oracle.direct(3, m.x, m.elems, ot)
+    rg = oracle.adjoint(3, m.x, m.elems, ot, ws[k].cpu().numpy(), cs[k].cpu().numpy())
+    o = [a.cpu().numpy() for a in b.outs[k]]
+    assert np.abs(o[0] - rn).max() <= 1e-12 * m.h ** 2
+    assert np.abs(o[1] - rv).max() <= 1e-12 * m.h ** 3
+    assert np.abs(o[2] - rb).max() <= 1e-12 * m.h ** 2
+    assert np.abs(o[3] - rg).max() <= 1e-12 * np.abs(rg).max()

@@ -4,11 +4,13 @@
 launch configuration (fused tiled scatter, one launch per step, at the tile
 sizes the autotuner picks there: 256 nodes for DW and FP64, which run
 512-thread CTAs with the L2 prefetch of the next tile, 128 for MIXED; the
-ordered gather path for comparison): edge_build is checked through properties that characterise
-the sorted unique edge list exactly; the metrics and the adjoint are checked
-at 2000 sampled edges and nodes, each computed by the oracle alone from the
-elements around it.  96^3 x 6 (the adjoint workload): the full gradient
-against the oracle's analytic gradient and central differences on 1000 nodes.
+ordered gather path and the atomic scatter for comparison): the topology is
+compared with the oracle's bit for bit, and every directed area, dual
+volume, boundary normal and gradient component with one full oracle run.
+96^3 x 6 (the adjoint workload): the full gradient against the oracle's
+analytic gradient and central differences on 1000 nodes.  The paper's own
+grid sizes: 255^2 x 2 triangles in full, 256^3 x 6 tets sampled, with
+closure and the volume sum at every node.
 """
 import os
 
@@ -31,87 +33,98 @@ def _mesh(name):
     return meshgen.generate.cached_workload(name, cache_dir=cache)
 
 
+class Full:
+    """The 160^3 grid on the GPU and one full oracle evaluation of it."""
+
+
 @pytest.fixture(scope="module")
 def big():
     from paper_2502_00778_gb300 import api
-    m = _mesh("kuhn160_off1e3")
-    x = torch.from_numpy(m.x).to(DEV)
-    el = torch.from_numpy(m.elems).to(DEV)
-    topo = api.edge_build(el, x)
-    api.plan_build(topo, 256)
-    return m, x, topo
+    f = Full()
+    f.m = m = _mesh("kuhn160_off1e3")
+    f.x = torch.from_numpy(m.x).to(DEV)
+    f.topo = api.edge_build(torch.from_numpy(m.elems).to(DEV), f.x)
+    # the oracle's own topology, metrics and gradient (about two minutes of
+    # serial CPU work); the loss weights are counter-based functions of the
+    # node ids of each edge (the oracle's edge list)
+    f.ot = oracle.topology(3, m.elems, m.x)
+    f.rn, f.rv, f.rb = oracle.direct(3, m.x, m.elems, f.ot)
+    f.w, f.c = meshgen.generate.hash_weights(f.ot.edges, m.n_nodes, 3, SEED)
+    f.rg = oracle.adjoint(3, m.x, m.elems, f.ot, f.w, f.c)
+    f.wt, f.ct = torch.from_numpy(f.w).to(DEV), torch.from_numpy(f.c).to(DEV)
+    return f
 
 
 # tile_nodes per (form, path) as the benchmark's autotuner picks them
 TILE = {("dw", "tiled"): 256, ("fp64", "tiled"): 256, ("mixed", "tiled"): 128, ("dw", "gather"): 128}
 
 
-def test_edge_build_properties_160(big):
-    m, x, topo = big
+def test_edge_build_160(big):
+    """Edges, element->edge map, boundary faces (outward order and owner)
+    and boundary nodes equal the oracle's bit for bit; the counts equal the
+    closed forms of the structured grid."""
+    m, topo, ot = big.m, big.topo, big.ot
     n = 160
-    e = topo.edges.cpu().numpy().astype(np.int64)
-    assert e.shape[0] == 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3
-    assert np.all(e[:, 0] < e[:, 1])
-    key = e[:, 0] * m.n_nodes + e[:, 1]
-    assert np.all(np.diff(key) > 0)                      # sorted, unique
-    e2e = topo.elem2edge.cpu().numpy()
-    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
-    used = np.zeros(e.shape[0], bool)
-    for l, (p, q) in enumerate(pairs):
-        a, b = m.elems[:, p].astype(np.int64), m.elems[:, q].astype(np.int64)
-        lo, hi = np.minimum(a, b), np.maximum(a, b)
-        assert np.array_equal(e[e2e[:, l], 0], lo) and np.array_equal(e[e2e[:, l], 1], hi)
-        used[e2e[:, l]] = True
-    assert used.all()                                    # exactly the element edges
-    assert topo.n_bfaces == 12 * n * n
-    assert topo.n_bnodes == (n + 1) ** 3 - (n - 1) ** 3
+    assert np.array_equal(topo.edges.cpu().numpy(), ot.edges)
+    assert np.array_equal(topo.elem2edge.cpu().numpy(), ot.elem2edge)
+    assert np.array_equal(topo.bface.cpu().numpy(), ot.bface)
+    assert np.array_equal(topo.bface_owner.cpu().numpy(), ot.bowner)
+    assert np.array_equal(topo.bnode.cpu().numpy(), ot.bnode)
+    assert ot.n_edges == 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3
+    assert ot.bface.shape[0] == 12 * n * n
+    assert ot.bnode.size == (n + 1) ** 3 - (n - 1) ** 3
+
+
+def _closure_and_volume(m, edges, bnode, n, v, b):
+    """max |sum of outward directed areas + bnormal| over all nodes, and the
+    volume sum, accumulated with numpy.bincount."""
+    d = m.dim
+    a = np.zeros((m.n_nodes, d))
+    for k in range(d):
+        a[:, k] = (np.bincount(edges[:, 0], weights=n[:, k], minlength=m.n_nodes) -
+                   np.bincount(edges[:, 1], weights=n[:, k], minlength=m.n_nodes))
+    a[bnode] += b
+    return np.abs(a).max(), v.sum()
 
 
 @pytest.mark.parametrize("prec,path", [("dw", "tiled"), ("fp64", "tiled"), ("mixed", "tiled"), ("dw", "gather")])
-def test_sampled_parity_160(big, prec, path):
+def test_full_parity_160(big, prec, path):
+    """Every output of the fused forward + adjoint step against the oracle,
+    element by element (FP64 contract: |dn| <= 1e-12 h^2, |dV| <= 1e-12 h^3,
+    |dbnormal| <= 1e-12 h^2, |dgrad| <= 1e-12 max|grad| of the oracle; the
+    FP32 element-math form at its stated accuracy)."""
     from paper_2502_00778_gb300 import api
-    m, x, topo = big
-    e = topo.edges.cpu().numpy()
-    rng = np.random.Generator(np.random.PCG64(SEED + 31))
-    es = np.sort(rng.choice(e.shape[0], 2000, replace=False))
-    bn = topo.bnode.cpu().numpy()
-    ns = np.unique(np.concatenate([rng.choice(m.n_nodes, 1500, replace=False), rng.choice(bn, 500, replace=False)]))
-    w, c = meshgen.generate.hash_weights(e, m.n_nodes, 3, SEED)
-    wt, ct = torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV)
+    m, x, topo = big.m, big.x, big.topo
     api.plan_build(topo, TILE[(prec, path)])
-    n, v, b, g = api.edge_metrics_fused(topo, x, wt, ct, prec, path=path)
-    rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], ns, SEED)
+    n, v, b, g = api.edge_metrics_fused(topo, x, big.wt, big.ct, prec, path=path)
+    n, v, b, g = n.cpu().numpy(), v.cpu().numpy(), b.cpu().numpy(), g.cpu().numpy()
     h = m.h
-    # FP64 contract; the FP32 element-math form at its stated accuracy
     tn, tv, tg = (1e-12, 1e-12, 1e-12) if prec != "mixed" else (2e-6, 2e-6, 1e-5)
-    assert np.abs(n.cpu().numpy()[es] - rn).max() <= tn * h * h
-    assert np.abs(v.cpu().numpy()[ns] - rv).max() <= tv * h ** 3
-    bfull = np.zeros((m.n_nodes, 3))
-    bfull[bn] = b.cpu().numpy()
-    assert np.abs(bfull[ns] - rb).max() <= tn * h * h
-    gg = g.cpu().numpy()
-    assert np.abs(gg[ns] - rg).max() <= tg * np.abs(gg).max()
+    gmax = np.abs(big.rg).max()
+    assert np.abs(n - big.rn).max() <= tn * h * h
+    assert np.abs(v - big.rv).max() <= tv * h ** 3
+    assert np.abs(b - big.rb).max() <= tn * h * h
+    assert np.abs(g - big.rg).max() <= tg * gmax
     if prec == "mixed":
         return
     # properties at every node: closure and the volume sum
-    a = np.zeros((m.n_nodes, 3))
-    nn = n.cpu().numpy()
-    np.add.at(a, e[:, 0], nn)
-    np.add.at(a, e[:, 1], -nn)
-    a[bn] += bfull[bn]
-    assert np.abs(a).max() <= 1e-12 * h * h
-    assert abs(v.cpu().numpy().sum() - 1.0) <= 1e-11
+    cl, vs = _closure_and_volume(m, big.ot.edges, big.ot.bnode, n, v, b)
+    assert cl <= 1e-12 * h * h
+    assert abs(vs - 1.0) <= 1e-11
 
 
-def test_atomic_fp64_sampled_160(big):
+def test_atomic_fp64_160(big):
+    """The atomic scatter in native FP64: every n, V, bnormal and gradient
+    component against the oracle."""
     from paper_2502_00778_gb300 import api
-    m, x, topo = big
-    e = topo.edges.cpu().numpy()
-    rng = np.random.Generator(np.random.PCG64(SEED + 32))
-    es = np.sort(rng.choice(e.shape[0], 500, replace=False))
+    m, x, topo = big.m, big.x, big.topo
     n, v, b = api.edge_metrics(topo, x, "fp64", "atomic")
-    rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], np.array([0], np.int32), SEED)
-    assert np.abs(n.cpu().numpy()[es] - rn).max() <= 1e-12 * m.h ** 2
+    g = api.edge_metrics_adjoint(topo, x, big.wt, big.ct, "fp64", "atomic")
+    h = m.h
+    assert np.abs(n.cpu().numpy() - big.rn).max() <= 1e-12 * h * h
+    assert np.abs(v.cpu().numpy() - big.rv).max() <= 1e-12 * h ** 3
+    assert np.abs(b.cpu().numpy() - big.rb).max() <= 1e-12 * h * h
+    assert np.abs(g.cpu().numpy() - big.rg).max() <= 1e-12 * np.abs(big.rg).max()
 
 
 def test_adjoint_96_fd():
@@ -162,3 +175,56 @@ def test_paper_2d_grid_size():
     assert np.abs(g.cpu().numpy() - rg).max() <= 1e-12 * np.abs(rg).max()
     n2, v2, b2 = api.edge_metrics(topo, x, "fp64", "csr")
     assert np.array_equal(n2.cpu().numpy(), rn) and np.array_equal(v2.cpu().numpy(), rv)
+
+
+def test_paper_3d_grid_size_256():
+    """The paper's 3D grid size (Sec. 5, Table of n_jk and V_j timings:
+    256^3 x 6 = 100,663,296 tets, 16,974,593 nodes) in the benchmark's launch
+    configuration (fused DW step, 256-node tiles): topology by the
+    properties that characterise the sorted unique edge list, n and the
+    node outputs against the oracle at 2000 sampled edges and 2000 sampled
+    nodes (each evaluated by the oracle from the elements around it), and
+    closure and the volume sum at every node."""
+    from paper_2502_00778_gb300 import api
+    m = _mesh("kuhn256")
+    n_c = 256
+    assert (m.n_nodes, m.n_elems) == (16974593, 100663296)
+    x = torch.from_numpy(m.x).to(DEV)
+    topo = api.edge_build(torch.from_numpy(m.elems).to(DEV), x)
+    e = topo.edges.cpu().numpy()
+    assert e.shape[0] == 3 * n_c * (n_c + 1) ** 2 + 3 * n_c * n_c * (n_c + 1) + n_c ** 3
+    assert np.all(e[:, 0] < e[:, 1])
+    key = e[:, 0].astype(np.int64) * m.n_nodes + e[:, 1]
+    assert np.all(np.diff(key) > 0)
+    e2e = topo.elem2edge.cpu().numpy()
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    used = np.zeros(e.shape[0], bool)
+    for l, (p, q) in enumerate(pairs):
+        a, b2 = m.elems[:, p], m.elems[:, q]
+        assert np.array_equal(e[e2e[:, l], 0], np.minimum(a, b2)) and np.array_equal(e[e2e[:, l], 1],
+                                                                                     np.maximum(a, b2))
+        used[e2e[:, l]] = True
+    assert used.all()
+    del e2e, used, key
+    assert topo.n_bfaces == 12 * n_c * n_c and topo.n_bnodes == (n_c + 1) ** 3 - (n_c - 1) ** 3
+    bn = topo.bnode.cpu().numpy()
+    w, c = meshgen.generate.hash_weights(e, m.n_nodes, 3, SEED)
+    api.plan_build(topo, 256)
+    n, v, b, g = api.edge_metrics_fused(topo, x, torch.from_numpy(w).to(DEV), torch.from_numpy(c).to(DEV), "dw",
+                                        path="tiled")
+    del w, c
+    n, v, b, g = n.cpu().numpy(), v.cpu().numpy(), b.cpu().numpy(), g.cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(SEED + 33))
+    es = np.sort(rng.choice(e.shape[0], 2000, replace=False))
+    ns = np.unique(np.concatenate([rng.choice(m.n_nodes, 1500, replace=False), rng.choice(bn, 500, replace=False)]))
+    rn, rv, rb, rg = oracle.sample(3, m.x, m.elems, e[es, 0], e[es, 1], ns, SEED)
+    h = m.h
+    assert np.abs(n[es] - rn).max() <= 1e-12 * h * h
+    assert np.abs(v[ns] - rv).max() <= 1e-12 * h ** 3
+    bfull = np.zeros((m.n_nodes, 3))
+    bfull[bn] = b
+    assert np.abs(bfull[ns] - rb).max() <= 1e-12 * h * h
+    assert np.abs(g[ns] - rg).max() <= 1e-12 * np.abs(rg).max()
+    cl, vs = _closure_and_volume(m, e, bn, n, v, b)
+    assert cl <= 1e-12 * h * h
+    assert abs(vs - 1.0) <= 1e-11

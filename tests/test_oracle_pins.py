@@ -213,6 +213,58 @@ def test_closure_volume_and_exactness(builder):
     assert np.abs(resid).max() <= 1e-12 * m.h ** d * (1e3 if m.meta.get("offset") else 1)
 
 
+@pytest.mark.parametrize("builder", [
+    lambda: meshgen.tri_square(8, jitter=0.3, seed=24),
+    lambda: meshgen.kuhn_cube(4, jitter=0.3, seed=25),
+    lambda: meshgen.kuhn_cube(3, jitter=0.2, seed=26, offset=1000.0),
+    lambda: meshgen.single_simplex(3),
+])
+def test_closure_function(builder):
+    """or_closure (Sec. 3.2.3: sum over a node's edges of the outward directed
+    areas plus (1/D) times the area vectors of its boundary faces) against
+    the same sum done here in numpy, with face vectors from numpy cross
+    products, for arbitrary edge values; zero at every node for the oracle's
+    own n; and a planted change of one edge value moves the sums of exactly
+    that edge's two nodes, by + and - the change."""
+    m = builder()
+    d = m.dim
+    t, n, v, b = _metrics(m)
+    rng = np.random.Generator(np.random.PCG64(7))
+    # arbitrary edge values: the edge loop and the boundary term, independently
+    r = rng.standard_normal(n.shape)
+    ref = _outward_sums(m, t, r)
+    for f in t.bface:
+        P = m.x[f]
+        if d == 3:
+            nB = 0.5 * np.cross(P[1] - P[0], P[2] - P[0])
+        else:
+            nB = np.array([P[0, 1] - P[1, 1], P[1, 0] - P[0, 0]])
+        ref[f] += nB / d
+    got = oracle.closure(d, m.x, t, r)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+    # the oracle's own directed areas close at every node
+    a = oracle.closure(d, m.x, t, n)
+    hs = m.h ** (d - 1) if m.n_elems > 1 else 1.0
+    assert np.abs(a).max() <= 1e-13 * hs * (1e3 if m.meta.get("offset") else 1)
+    # the boundary term is the returned bnormal: closure = edge sums + bnormal
+    a2 = _outward_sums(m, t, n)
+    a2[t.bnode] += b
+    np.testing.assert_allclose(a, a2, rtol=0, atol=1e-13 * hs * (1e3 if m.meta.get("offset") else 1))
+    # planted change of one edge value
+    e = int(rng.integers(t.n_edges))
+    delta = np.arange(1, d + 1, dtype=np.float64) * 0.125
+    n2 = n.copy()
+    n2[e] += delta
+    a3 = oracle.closure(d, m.x, t, n2)
+    j, k = t.edges[e]
+    exp = a.copy()
+    exp[j] += delta
+    exp[k] -= delta
+    np.testing.assert_allclose(a3, exp, rtol=0, atol=1e-13)
+    moved = np.flatnonzero(np.abs(a3 - a).max(axis=1) > 1e-3)
+    assert sorted(moved.tolist()) == sorted([int(j), int(k)])
+
+
 def _cayley_menger(m):
     d = m.dim
     P = m.x[m.elems[:, :d + 1]]
