@@ -430,8 +430,11 @@ __global__ void k_bw_map(int64_t nbn, const int32_t* __restrict__ bnode, int32_t
 // order-preserving key (upper word of |v|) of the largest |bw| component
 __global__ void k_bw_maxkey(int64_t m, const double* __restrict__ bw, unsigned* __restrict__ key) {
     unsigned k = 0u;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
-        k = max(k, (unsigned)((unsigned long long)__double_as_longlong(bw[i]) >> 32) & 0x7fffffffu);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x) {
+        // non-finite weights stay out of the bound (their targets become NaN)
+        const unsigned ki = (unsigned)((unsigned long long)__double_as_longlong(bw[i]) >> 32) & 0x7fffffffu;
+        k = max(k, ki < 0x7ff00000u ? ki : 0u);
+    }
     k = __reduce_max_sync(0xffffffffu, k);
     if ((threadIdx.x & 31) == 0) atomicMax(key, k);
 }

@@ -115,12 +115,14 @@ __device__ __forceinline__ void dw_acc_f(dw& acc, float v) {
 }
 
 // double -> DW (truncated high part, remaining bits in the low part);
-// values below 2^-126 in magnitude map to 0
+// values below 2^-126 in magnitude map to 0; NaN, infinities and finite
+// values of magnitude 2^128 or more (outside the float range) map to NaN
 __device__ __forceinline__ dw dw_from_double(double d) {
     unsigned long long b = (unsigned long long)__double_as_longlong(d);
     int e = (int)((b >> 52) & 0x7ff);
     int ef = e - 1023 + 127;
     if (ef <= 0) return {0.f, 0.f};
+    if (ef >= 255) return {__int_as_float(0x7fc00000), __int_as_float(0x7fc00000)};
     unsigned sign = (unsigned)(b >> 63) << 31;
     float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffff));
     unsigned r = (unsigned)(b & 0x1fffffffu);
@@ -133,7 +135,8 @@ __device__ __forceinline__ dw dw_from_double(double d) {
 // double -> float by truncation of the mantissa (integer pipe only)
 __device__ __forceinline__ float f_from_double(double d) { return dw_from_double(d).h; }
 
-// DW -> double, correctly rounded up to one ulp, without FP64 instructions
+// DW -> double, correctly rounded up to one ulp, without FP64 instructions;
+// a non-finite sum gives NaN
 __device__ __forceinline__ double dw_to_double(dw a) {
     float s, e;
     two_sum(a.h, a.l, s, e);
@@ -142,6 +145,7 @@ __device__ __forceinline__ double dw_to_double(dw a) {
     unsigned sign = sb >> 31;
     int ex = (int)((sb >> 23) & 0xff);
     if (ex == 0) return 0.0;
+    if (ex == 255 || e != e) return __longlong_as_double(0x7ff8000000000000LL);
     long long M = (1LL << 52) | ((long long)(sb & 0x7fffff) << 29);
     int k = 0;
     int sc = 306 - ex;                      // e * 2^(179 - ex): e in units of the double ulp of s
@@ -160,11 +164,13 @@ __device__ __forceinline__ double dw_to_double(dw a) {
     return __longlong_as_double((long long)bits);
 }
 
-// float -> double on the integer pipe (exact)
+// float -> double on the integer pipe (exact; denormals map to 0, NaN and
+// infinities to NaN)
 __device__ __forceinline__ double f_to_double(float f) {
     unsigned b = __float_as_uint(f);
     int ex = (int)((b >> 23) & 0xff);
     if (ex == 0) return 0.0;
+    if (ex == 255) return __longlong_as_double(0x7ff8000000000000LL);
     unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ex - 127 + 1023) << 52) |
                               ((unsigned long long)(b & 0x7fffff) << 29);
     return __longlong_as_double((long long)bits);

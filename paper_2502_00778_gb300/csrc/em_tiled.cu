@@ -122,6 +122,30 @@ struct Form<EM_PREC_MIXED> {
 
 enum { DO_FWD = 1, DO_ADJ = 2 };
 
+// NaN tests of staged values (staging turns every non-finite input into NaN)
+__device__ __forceinline__ bool is_nan(double v) { return v != v; }
+__device__ __forceinline__ bool is_nan(float v) { return v != v; }
+__device__ __forceinline__ bool is_nan(dw v) { return v.h != v.h; }
+__device__ __forceinline__ double qnan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
+// FP64 form: infinities become NaN too (the FP32-based forms' conversions
+// already map every non-finite or out-of-range value to NaN)
+__device__ __forceinline__ double finite_or_nan(double v) { return isfinite(v) ? v : qnan_d(); }
+__device__ __forceinline__ float finite_or_nan(float v) { return v; }
+__device__ __forceinline__ dw finite_or_nan(dw v) { return v; }
+
+// The tile's coordinate origin, per component: the first owned node whose
+// coordinate is finite (0 if none is), so that one non-finite coordinate does
+// not reach the other staged nodes through the subtraction.
+template <int DIM>
+__device__ __forceinline__ void tile_origin(const double* x, int node0, int n_own, double* org) {
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        double o = x[int64_t(node0) * DIM + d];
+        for (int k = 1; !isfinite(o) && k < n_own; k++) o = x[(int64_t(node0) + k) * DIM + d];
+        org[d] = isfinite(o) ? o : 0.0;
+    }
+}
+
 // shared-memory layout, computed identically on host and device
 struct Smem {
     size_t xs, ws, cs, st_m, st_v, st_g, acc_e, cur_e, acc_v, acc_g, cur_n, acc_b, cur_b;
@@ -230,8 +254,7 @@ __device__ __forceinline__ void run_tile(const TileArgs& A, int t, char* smem) {
     constexpr int NCN = ((WHAT & DO_FWD) ? 1 : 0) + ((WHAT & DO_ADJ) ? DIM : 0);   // node: [grad comps..., V]
     constexpr int NCB = ((WHAT & DO_FWD) ? DIM : 0) + ((WHAT & DO_ADJ) ? DIM : 0);  // boundary node: [bnormal, grad]
     double org[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    tile_origin<DIM>(A.x, ti.node0, ti.n_own, org);
 
     // ---- stage coordinates (and w, c), reset accumulators ----------------
     for (int i = tid; i < nnodes; i += NT) {
@@ -633,11 +656,16 @@ __device__ __forceinline__ int sg_clamp(int sg, int lo, int hi) { return sg > hi
 // like their bit patterns, so an integer max gives the max magnitude.  Every
 // value with key k is below the double whose upper word is k + 1, and that
 // double is below 2^key_exp(k).  Integer pipe only, and valid over the whole
-// finite double range.
+// finite double range.  NaN and infinities get key 0, so they never enter a
+// maximum: the scales bound the finite values, and the outputs that depend on
+// a non-finite input are set to NaN separately (see the poison pass below).
+// key_exp therefore only sees keys below 0x7ff00000 (exponents up to 1025).
 __device__ __forceinline__ unsigned mkey(double v) {
-    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+    const unsigned k = (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+    return k < 0x7ff00000u ? k : 0u;
 }
 __device__ __forceinline__ int key_exp(unsigned k) { return (int)(((k + 1u) >> 20) & 0x7ffu) - 1022; }
+
 
 template <int PREC>
 struct Fix;
@@ -657,7 +685,8 @@ struct Fix<EM_PREC_FP64> {
 
 template <>
 struct Fix<EM_PREC_DW> {
-    static constexpr int NL = 3, TOP = 62, LO = -60, HI = 120;
+    // LO, HI: the float powers of two 2^(sg - 42) and 2^(sg - 21) below stay normal
+    static constexpr int NL = 3, TOP = 62, LO = -80, HI = 148;
     static __device__ __forceinline__ Lq q(dw v, int sg) {
         float r;
         const float th = __fmul_rn(v.h, pow2f(sg - 42));
@@ -680,7 +709,7 @@ struct Fix<EM_PREC_DW> {
 
 template <>
 struct Fix<EM_PREC_MIXED> {
-    static constexpr int NL = 2, TOP = 41, LO = -80, HI = 120;
+    static constexpr int NL = 2, TOP = 41, LO = -80, HI = 148;
     static __device__ __forceinline__ Lq q(float v, int sg) {
         float r;
         const int a = fx_round(__fmul_rn(v, pow2f(sg - 21)), r);
@@ -804,7 +833,7 @@ __host__ __device__ inline SmemS smem_layout_s(const Dims& D) {
     s.acc_g = (WHAT & DO_ADJ) ? take(wb * DIM * D.max_own) : 0;
     s.acc_b = (WHAT & DO_FWD) ? take(wb * DIM * D.max_bo) : 0;
     s.bmap = take(sizeof(int) * D.max_own);
-    s.red = take(sizeof(unsigned) * (16 + 4 * RED_WARPS));
+    s.red = take(sizeof(unsigned) * (16 + 5 * RED_WARPS));
     s.total = (o + 15) & ~size_t(15);
     return s;
 }
@@ -871,13 +900,13 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
 
     // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
     double org[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    tile_origin<DIM>(A.x, ti.node0, ti.n_own, org);
     // gathers are issued in batches of SB per thread so that several loads are
     // in flight before the first one is used
     constexpr int SB = 4, SBW = 8;
     unsigned wm = 0u, cm = 0u;
     float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
+    bool nf = false;     // a staged value is non-finite (staged as NaN)
     for (int i0 = tid; i0 < nnodes; i0 += SB * NTH) {
         int64_t v[SB];
 #pragma unroll
@@ -899,13 +928,15 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
             const int i = i0 + u * NTH;
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
-                const C xc = F::coord(xv[u][d], org[d]);
+                const C xc = finite_or_nan(F::coord(xv[u][d], org[d]));
                 xs[i * DIM + d] = xc;
+                nf |= is_nan(xc);
                 if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
             }
             if (WHAT & DO_ADJ) {
-                const V c1 = F::from_double(cv[u]);
+                const V c1 = finite_or_nan(F::from_double(cv[u]));
                 cs[i] = c1;
+                nf |= is_nan(c1);
                 cm = max(cm, FX::mag(c1));
             }
         }
@@ -931,8 +962,9 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                 const int i = i0 + u * NTH;
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
-                    const V w1 = F::from_double(wv[u][d]);
+                    const V w1 = finite_or_nan(F::from_double(wv[u][d]));
                     ws[i * DIM + d] = w1;
+                    nf |= is_nan(w1);
                     wm = max(wm, FX::mag(w1));
                 }
             }
@@ -943,6 +975,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
         block_max(wred, 2, cm);
     }
     if constexpr (PREC != EM_PREC_FP64) block_max(wred, 3, mkey(f_to_double(xl)));
+    block_max(wred, 4, nf ? 1u : 0u);
     __syncthreads();
     for (int k = tid; k < ti.n_bo; k += NTH) bmap[A.bnode[ti.bnode0 + k] - ti.node0] = k;
 
@@ -1005,10 +1038,22 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     // 3D: |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3 < 8 Lx^3,
     // |n_B| <= 8 Lx^2 with up to 3 boundary faces per element at a node;
     // 2D: |n_i| <= 2 Lx, |det| <= 2 Lx^2, boundary edge <= 2 Lx
-    const int sg_e = sg_clamp(TP - (DIM == 3 ? 5 + 2 * eL + eKe : 3 + eL + eKe), LO, HI);
-    const int sg_v = sg_clamp(TP - (DIM == 3 ? 3 + 3 * eL + eKv : 4 + 2 * eL + eKv), LO, HI);
-    const int sg_b = sg_clamp(TP - (DIM == 3 ? 5 + 2 * eL + eKv : 3 + eL + eKv), LO, HI);
+    const int u_e = TP - (DIM == 3 ? 5 + 2 * eL + eKe : 3 + eL + eKe);
+    const int u_v = TP - (DIM == 3 ? 3 + 3 * eL + eKv : 4 + 2 * eL + eKv);
+    const int u_b = TP - (DIM == 3 ? 5 + 2 * eL + eKv : 3 + eL + eKv);
+    const int sg_e = sg_clamp(u_e, LO, HI), sg_v = sg_clamp(u_v, LO, HI), sg_b = sg_clamp(u_b, LO, HI);
     const int sg_g = (WHAT & DO_ADJ) ? sg_clamp(TP - eg, LO, HI) : 0;
+    // Element extents outside the form's range (a scale outside [LO, HI]:
+    // the values would overflow the fixed point, or lose the digits the
+    // contract needs) make every output of the tile NaN instead of silently
+    // wrong; for the FP32-based forms that is an element extent outside about
+    // 2^-34 .. 2^40, for the FP64 form outside about 2^-290 .. 2^290.  A tile
+    // whose elements all have zero extent contributes exact zeros at any scale.
+    // Non-finite staged values mark the tile for the poison pass below.
+    const bool lx0 = red_max(wred, 0, NW) == 0u;
+    const bool range_bad = (!lx0 && (u_e < LO || u_e > HI || u_v < LO || u_v > HI || u_b < LO || u_b > HI)) ||
+                           ((WHAT & DO_ADJ) && TP - eg < LO);
+    const bool nf_tile = red_max(wred, 4, NW) != 0u;
     if ((tid >> 5) == (NTH >> 5) - 1) pf(tid & 31);
 
     // ---- elements: compute and scatter to owned targets -------------------
@@ -1269,6 +1314,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                     }
 #pragma unroll
                     for (int d = 0; d < 3; d++) K[d] = F::from_double(Kd[d] / 3.0);
+                    if (!(isfinite(Kd[0]) && isfinite(Kd[1]) && isfinite(Kd[2]))) atomicOr(red + 11, 1u);
                 }
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
@@ -1312,6 +1358,7 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
                     }
                     gx = F::add(gx, F::from_double(0.5 * Kd[1]));
                     gy = F::add(gy, F::from_double(-0.5 * Kd[0]));
+                    if (!(isfinite(Kd[0]) && isfinite(Kd[1]))) atomicOr(red + 11, 1u);
                 }
                 if (f.v[1] < ti.n_own) {
                     acc_add<NL>(acc_g, sgs, f.v[1] * 2, FX::q(gx, sg_g));
@@ -1326,19 +1373,116 @@ __device__ __forceinline__ void run_tile_scatter(const TileArgs& A, int t, char*
     }
     __syncthreads();
 
+    // ---- non-finite inputs (rare; tile-uniform branch) -----------------------
+    // Every output to which an element or boundary face with a non-finite
+    // input contributes is NaN: forward outputs (n, V, bnormal) from the
+    // coordinates, gradients from the coordinates, w, c and the boundary-normal
+    // weights.  Such contributions went into the integer sums as arbitrary
+    // values (the scales above bound the finite ones only); their targets are
+    // marked with a first-limb value no sum can reach (|limb sums| < 2^31 by
+    // the headroom argument above) and written as NaN.
+    constexpr int MARK = -2147483647 - 1;
+    const bool poison = nf_tile || (red[11] != 0u);
+    if (poison && !range_bad) {
+        constexpr int NLE = DIM == 3 ? 6 : 3;
+        for (int i = tid; i < ti.n_el; i += NTH) {
+            const ElemConn cn = conn[i];
+            const ElemEdges ee = tedge[i];
+            bool px = false, pa = false;
+#pragma unroll
+            for (int r = 0; r <= DIM; r++)
+#pragma unroll
+                for (int d = 0; d < DIM; d++) px |= is_nan(xs[cn.v[r] * DIM + d]);
+            if (WHAT & DO_ADJ) {
+#pragma unroll
+                for (int l = 0; l < NLE; l++)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) pa |= is_nan(ws[ee.e[l] * DIM + d]);
+#pragma unroll
+                for (int r = 0; r <= DIM; r++) pa |= is_nan(cs[cn.v[r]]);
+            }
+            pa |= px;
+            if ((WHAT & DO_FWD) && px) {
+#pragma unroll
+                for (int l = 0; l < NLE; l++)
+                    if (ee.e[l] < ti.n_eo)
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) acc_e[ee.e[l] * DIM + d] = MARK;
+#pragma unroll
+                for (int r = 0; r <= DIM; r++)
+                    if (cn.v[r] < ti.n_own) acc_v[cn.v[r]] = MARK;
+            }
+            if ((WHAT & DO_ADJ) && pa) {
+#pragma unroll
+                for (int r = 0; r <= DIM; r++)
+                    if (cn.v[r] < ti.n_own)
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) acc_g[cn.v[r] * DIM + d] = MARK;
+            }
+        }
+        for (int j = tid; j < ti.n_bf; j += NTH) {
+            const TileBFace f = tbf[j];
+            constexpr int FE = DIM == 3 ? 3 : 1;
+            bool px = false, pa = false;
+#pragma unroll
+            for (int k = 0; k < DIM; k++)
+#pragma unroll
+                for (int d = 0; d < DIM; d++) px |= is_nan(xs[f.v[k] * DIM + d]);
+            if (WHAT & DO_ADJ) {
+#pragma unroll
+                for (int k = 0; k < FE; k++)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) pa |= is_nan(ws[f.e[k] * DIM + d]);
+                if (A.bwa.bw) {
+#pragma unroll
+                    for (int k = 0; k < DIM; k++) {
+                        const int lv = f.v[k];
+                        const int64_t gv = lv < ti.n_own ? int64_t(ti.node0) + lv : int64_t(halo[lv - ti.n_own]);
+                        const int64_t b = A.bwa.map[gv];
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) pa |= !isfinite(A.bwa.bw[DIM * b + d]);
+                    }
+                }
+            }
+            pa |= px;
+            if ((WHAT & DO_FWD) && px) {
+#pragma unroll
+                for (int k = 0; k < FE; k++)
+                    if (f.e[k] < ti.n_eo)
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) acc_e[f.e[k] * DIM + d] = MARK;
+#pragma unroll
+                for (int k = 0; k < DIM; k++)
+                    if (f.v[k] < ti.n_own && bmap[f.v[k]] >= 0)
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) acc_b[bmap[f.v[k]] * DIM + d] = MARK;
+            }
+            if ((WHAT & DO_ADJ) && pa) {
+#pragma unroll
+                for (int k = 0; k < DIM; k++)
+                    if (f.v[k] < ti.n_own)
+#pragma unroll
+                        for (int d = 0; d < DIM; d++) acc_g[f.v[k] * DIM + d] = MARK;
+            }
+        }
+        __syncthreads();
+    }
+
     const double esc = DIM == 3 ? 1.0 / 12.0 : 1.0 / 3.0;
     const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
     const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
+    // out(p, q): output q of the planes p at scale sg, NaN where marked
+    auto outv = [&](const int* p, int stride, int q, int sg, double sc) {
+        if (range_bad || (poison && p[q] == MARK)) return qnan_d();
+        return FX::out(acc_load<NL>(p, stride, q), sg, sc);
+    };
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < ti.n_eo * DIM; q += NTH)
-            A.n_out[int64_t(ti.edge0) * DIM + q] = FX::out(acc_load<NL>(acc_e, se, q), sg_e, esc);
-        for (int q = tid; q < ti.n_bo * DIM; q += NTH)
-            A.bnormal[int64_t(ti.bnode0) * DIM + q] = FX::out(acc_load<NL>(acc_b, sb, q), sg_b, bsc);
-        for (int q = tid; q < ti.n_own; q += NTH) A.vol[int64_t(ti.node0) + q] = FX::out(acc_load<NL>(acc_v, sv, q), sg_v, vsc);
+        for (int q = tid; q < ti.n_eo * DIM; q += NTH) A.n_out[int64_t(ti.edge0) * DIM + q] = outv(acc_e, se, q, sg_e, esc);
+        for (int q = tid; q < ti.n_bo * DIM; q += NTH) A.bnormal[int64_t(ti.bnode0) * DIM + q] = outv(acc_b, sb, q, sg_b, bsc);
+        for (int q = tid; q < ti.n_own; q += NTH) A.vol[int64_t(ti.node0) + q] = outv(acc_v, sv, q, sg_v, vsc);
     }
     if (WHAT & DO_ADJ)
-        for (int q = tid; q < ti.n_own * DIM; q += NTH)
-            A.grad[int64_t(ti.node0) * DIM + q] = FX::out(acc_load<NL>(acc_g, sgs, q), sg_g, 1.0);
+        for (int q = tid; q < ti.n_own * DIM; q += NTH) A.grad[int64_t(ti.node0) * DIM + q] = outv(acc_g, sgs, q, sg_g, 1.0);
 }
 
 // resident CTAs per SM the register allocation must allow: the forward alone
