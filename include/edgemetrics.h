@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define EM_VERSION 100
+#define EM_VERSION 200
 
 /* status codes */
 #define EM_OK               0
@@ -151,7 +151,7 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
                   void* stream);
 
 /* host summary of a plan (em_plan_build's plan_info output, em_mesh.plan_info) */
-#define EM_PLAN_INFO_LEN 16
+#define EM_PLAN_INFO_LEN 32
 #define EM_PLAN_INFO_TILE_NODES 0   /* nodes per tile */
 #define EM_PLAN_INFO_TILES      1   /* number of tiles */
 #define EM_PLAN_INFO_MAX_ELEMS  2   /* most elements in one tile */
@@ -167,6 +167,16 @@ int em_edge_build(int dim, int64_t n_nodes, int64_t n_elems,
 #define EM_PLAN_INFO_MAX_BSLOTS 12  /* most gather slots of one tile's boundary nodes */
 #define EM_PLAN_INFO_MAX_EDGE_VALENCE 13  /* most contributions to one edge (elements + boundary faces) */
 #define EM_PLAN_INFO_MAX_NODE_VALENCE 14  /* most elements around one node */
+/* scatter tiles (EM_PATH_TILED: each element computed once, by the tile of
+ * its lowest node; partial sums for other tiles' targets go out as records) */
+#define EM_PLAN_INFO_S_MAX_ELEMS  15  /* most elements of one scatter tile */
+#define EM_PLAN_INFO_S_MAX_NODES  16  /* most local nodes (owned + halo) */
+#define EM_PLAN_INFO_S_MAX_EDGES  17  /* most local edges (owned + halo) */
+#define EM_PLAN_INFO_S_MAX_BNODES 18  /* most local boundary nodes (owned + halo) */
+#define EM_PLAN_INFO_S_MAX_BFACES 19  /* most boundary faces of one scatter tile */
+#define EM_PLAN_INFO_REC_NODES    20  /* node records (halo nodes of all tiles) */
+#define EM_PLAN_INFO_REC_EDGES    21  /* edge records (halo edges of all tiles) */
+#define EM_PLAN_INFO_REC_BNODES   22  /* boundary-node records */
 
 /* em_plan_build -- tiled gather plan for EM_PATH_GATHER (run once per
  * connectivity, after em_edge_build).
@@ -360,6 +370,10 @@ typedef struct em_batch_item {
     em_mesh mesh;
     const double* x; const double* w; const double* c;
     double* n_edge; double* vol; double* bnormal; double* grad_x;
+    void* rec;   /* DEVICE scratch of this grid's tile records: 32 *
+                    (plan_info[EM_PLAN_INFO_REC_EDGES] + [REC_NODES] +
+                    [REC_BNODES]) bytes, 8-byte aligned, owned by the caller;
+                    no two items (and no concurrent call) may share one */
 } em_batch_item;
 
 /* Launch shapes of em_batched_fwd_adj (`blocks`). */

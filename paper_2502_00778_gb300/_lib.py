@@ -15,6 +15,9 @@ ERRORS = {
     -5: "EM_ERR_DEGENERATE", -6: "EM_ERR_TIMEOUT", -7: "EM_ERR_CAPACITY", -8: "EM_ERR_TOPOLOGY",
 }
 
+PLAN_INFO_LEN = 32
+PLAN_INFO = {"tile_nodes": 0, "tiles": 1, "rec_nodes": 20, "rec_edges": 21, "rec_bnodes": 22}
+
 PREC = {"fp64": 0, "dw": 1, "mixed": 2, "mixed_comp32": 3}
 PATH = {"atomic": 0, "gather": 1, "csr": 2, "tiled": 3}
 
@@ -32,7 +35,7 @@ class EmMesh(_c.Structure):
         ("elems", _vp), ("elem2edge", _vp), ("edges", _vp), ("edge_ptr", _vp), ("edge_slot", _vp),
         ("bface", _vp), ("bface_owner", _vp), ("bnode", _vp),
         ("plan", _vp), ("plan_bytes", _c.c_size_t),
-        ("plan_info", _c.c_int64 * 16),
+        ("plan_info", _c.c_int64 * PLAN_INFO_LEN),
     ]
 
 
@@ -41,6 +44,7 @@ class EmBatchItem(_c.Structure):
         ("mesh", EmMesh),
         ("x", _vp), ("w", _vp), ("c", _vp),
         ("n_edge", _vp), ("vol", _vp), ("bnormal", _vp), ("grad_x", _vp),
+        ("rec", _vp),
     ]
 
 

@@ -149,7 +149,7 @@ def plan_build(topo: Topology, tile_nodes: int = 0) -> Topology:
             _ptr(topo.edges), topo.n_bfaces, _ptr(topo.bface) if topo.n_bfaces else null,
             _ptr(topo.bface_owner) if topo.n_bfaces else null, topo.n_bnodes,
             _ptr(topo.bnode) if topo.n_bnodes else null, int(tile_nodes))
-    info = (ctypes.c_int64 * 16)()
+    info = (ctypes.c_int64 * _lib.PLAN_INFO_LEN)()
     # 1: scratch for the count pass; 2: exact plan and scratch sizes; 3: build
     check(L.em_plan_build(*args, null, ctypes.byref(wsb), null, ctypes.byref(pb), info, _stream()))
     ws = workspace.get(wsb.value, dev)
@@ -365,6 +365,7 @@ class Batch:
         self.precision = precision
         self.blocks = blocks
         self.outs = []
+        self.recs = []
         items = (_lib.EmBatchItem * len(topos))()
         for i, (t, x, w, c) in enumerate(zip(topos, xs, ws, cs)):
             d = t.dim
@@ -378,6 +379,11 @@ class Batch:
             items[i].c = c.data_ptr() if c is not None else None
             items[i].n_edge, items[i].vol = o[0].data_ptr(), o[1].data_ptr()
             items[i].bnormal, items[i].grad_x = o[2].data_ptr(), o[3].data_ptr()
+            # this grid's tile records (scatter tiles), 32 bytes each
+            nrec = sum(t.plan_info[_lib.PLAN_INFO[k]] for k in ("rec_edges", "rec_nodes", "rec_bnodes"))
+            r = torch.empty(max(32 * nrec, 256), dtype=torch.uint8, device=dev)
+            self.recs.append(r)
+            items[i].rec = r.data_ptr()
         raw = bytes(items)
         self.items = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
         tiles = [t.plan_info[1] for t in topos]
@@ -386,7 +392,7 @@ class Batch:
             prefix.append(prefix[-1] + n)
         self.n_tiles = prefix[-1]
         self.prefix = torch.tensor(prefix, dtype=torch.int64, device=dev)
-        self.max_info = (ctypes.c_int64 * 16)()
+        self.max_info = (ctypes.c_int64 * _lib.PLAN_INFO_LEN)()
         for t in topos:
             for k, v in enumerate(t.plan_info):
                 self.max_info[k] = max(self.max_info[k], v)

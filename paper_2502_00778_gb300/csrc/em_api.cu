@@ -97,7 +97,7 @@ int em_edge_metrics(const em_mesh* mesh, int precision, int path, const double* 
         if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
             return fail(EM_ERR_ARG, "gather/tiled paths support FP64, DW and MIXED");
         if (!mesh->plan) return fail(EM_ERR_ARG, "gather/tiled paths need a plan from em_plan_build");
-        need = gather_ws_bytes(mesh);
+        need = gather_ws_bytes(mesh, path == EM_PATH_TILED ? GATHER_SCATTER : 0);
     } else if (path == EM_PATH_CSR) {
         if (precision != EM_PREC_FP64) return fail(EM_ERR_ARG, "CSR path supports FP64 only");
         if (!mesh->edge_ptr || !mesh->edge_slot) return fail(EM_ERR_ARG, "CSR path needs edge_ptr and edge_slot");
@@ -136,7 +136,7 @@ int em_edge_metrics_adjoint(const em_mesh* mesh, int precision, int path, const 
         if (precision != EM_PREC_FP64 && precision != EM_PREC_DW && precision != EM_PREC_MIXED)
             return fail(EM_ERR_ARG, "gather/tiled adjoint supports FP64, DW and MIXED");
         if (!mesh->plan) return fail(EM_ERR_ARG, "gather/tiled paths need a plan from em_plan_build");
-        need = gather_ws_bytes(mesh);
+        need = gather_ws_bytes(mesh, path == EM_PATH_TILED ? GATHER_SCATTER : 0);
     } else {
         return fail(EM_ERR_ARG, "adjoint supports the ATOMIC, GATHER and TILED paths");
     }
@@ -172,7 +172,7 @@ int em_edge_metrics_fused(const em_mesh* mesh, int precision, int path, const do
     if (!mesh->plan) return fail(EM_ERR_ARG, "fused pass needs a plan from em_plan_build");
     if (bw && path == EM_PATH_GATHER)
         return fail(EM_ERR_ARG, "boundary-normal weights are supported by the TILED and ATOMIC paths");
-    const size_t bw_off = (gather_ws_bytes(mesh) + 255) & ~size_t(255);
+    const size_t bw_off = (gather_ws_bytes(mesh, path == EM_PATH_TILED ? GATHER_SCATTER : 0) + 255) & ~size_t(255);
     bool query;
     EM_TRY(check_ws(ws, ws_bytes, bw_off + bw_ws_bytes(mesh), &query));
     if (query) return ok();

@@ -33,7 +33,7 @@ namespace em {
 
 enum { GATHER_FWD = 1, GATHER_ADJ = 2, GATHER_SCATTER = 4 };
 
-size_t gather_ws_bytes(const em_mesh* m);
+size_t gather_ws_bytes(const em_mesh* m, int what);
 int gather_run(const em_mesh* m, int prec, int what, const double* x, const double* w, const double* c, double* n,
                double* vol, double* bnormal, double* g, void* ws, cudaStream_t s, const BwAux* bw = nullptr);
 
@@ -53,6 +53,11 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
                     const int32_t* bnode, int tile_nodes, void* ws, size_t* ws_bytes, void* plan, size_t* plan_bytes,
                     int64_t* plan_info, cudaStream_t s);
 int plan_tiles_impl(const void* plan, int64_t* n_tiles, cudaStream_t s);
+
+// scatter tiles (em_scatter.cu): workspace = the tiles' partial-sum records
+size_t scatter_ws_bytes(const em_mesh* m);
+int scatter_run(const em_mesh* m, int prec, int what, const double* x, const double* w, const double* c, double* n,
+                double* vol, double* bnormal, double* g, void* ws, cudaStream_t s, const BwAux* bw);
 
 int batched_impl(int n_meshes, const em_batch_item* items, const int64_t* tile_prefix, int64_t n_items,
                  const int64_t* max_info, int dim, int precision, int blocks, int32_t* status, void* ws,

@@ -421,6 +421,218 @@ __global__ void k_i64_to_i32(const int64_t* a, int64_t n, int32_t* b) {
     GRID_LOOP(i, n) b[i] = (int32_t)a[i];
 }
 
+// ---- scatter tiles ------------------------------------------------------------
+// element -> tile of its lowest node; key = tile << 5 | (element id mod 32):
+// a stable sort by it lists a tile's elements residue class by residue class
+// (ascending id inside a class), so the 32 elements a warp takes lie far
+// apart on the spatially ordered grid and rarely add into the same target in
+// one shared-memory atomic instruction.  Also counts, per element, the
+// candidates of the tile's halo lists (nodes and edges the tile does not own).
+__global__ void k_s_pairs(int dim, int64_t ne, const int32_t* elems, const int32_t* e2e, const int32_t* edges, int T,
+                          uint64_t* key, uint32_t* val, int32_t* tile_cnt, int32_t* hn, int32_t* he) {
+    const int nle = dim == 3 ? 6 : 3;
+    GRID_LOOP(E, ne) {
+        const int4 v4 = ld_el(elems, E);
+        int lo = v4.x;
+        for (int i = 1; i <= dim; i++) lo = min(lo, getc(v4, i));
+        const int a = lo / T;
+        key[E] = ((uint64_t)a << 5) | ((uint64_t)E & 31u);
+        val[E] = (uint32_t)E;
+        atomicAdd(&tile_cnt[a], 1);
+        int h = 0, g = 0;
+        for (int i = 0; i <= dim; i++) h += (getc(v4, i) / T != a);
+        for (int l = 0; l < nle; l++) g += (edges[2 * int64_t(e2e[E * nle + l])] / T != a);
+        hn[E] = h;
+        he[E] = g;
+    }
+}
+
+// candidates of the halo nodes (hk != NULL) or of the halo edges (hek != NULL)
+__global__ void k_s_halo(int dim, int64_t ne, const int32_t* elems, const int32_t* e2e, const int32_t* edges, int T,
+                         int bn, int be, const int64_t* hoff, const int64_t* heoff, uint64_t* hk, uint32_t* hv,
+                         uint64_t* hek, uint32_t* hev) {
+    const int nle = dim == 3 ? 6 : 3;
+    GRID_LOOP(E, ne) {
+        const int4 v4 = ld_el(elems, E);
+        int lo = v4.x;
+        for (int i = 1; i <= dim; i++) lo = min(lo, getc(v4, i));
+        const uint64_t a = (uint64_t)(lo / T);
+        if (hk) {
+            int64_t o = hoff[E];
+            for (int i = 0; i <= dim; i++) {
+                const int v = getc(v4, i);
+                if (v / T != (int)a) { hk[o] = (a << bn) | (uint64_t)v; hv[o] = 0; o++; }
+            }
+        }
+        if (hek) {
+            int64_t o = heoff[E];
+            for (int l = 0; l < nle; l++) {
+                const int32_t e = e2e[E * nle + l];
+                if (edges[2 * int64_t(e)] / T != (int)a) { hek[o] = (a << be) | (uint64_t)e; hev[o] = 0; o++; }
+            }
+        }
+    }
+}
+
+// tile of a boundary face's owner element (the owner's lowest node)
+__device__ __forceinline__ int face_tile(int dim, const int32_t* elems, const int32_t* bowner, int64_t B, int T) {
+    const int4 v4 = ld_el(elems, bowner[B] >> 2);
+    int lo = v4.x;
+    for (int i = 1; i <= dim; i++) lo = min(lo, getc(v4, i));
+    return lo / T;
+}
+
+__global__ void k_s_faces(int dim, int64_t nbf, const int32_t* elems, const int32_t* bface, const int32_t* bowner,
+                          int T, uint64_t* key, uint32_t* val, int32_t* tile_cnt, int32_t* hb) {
+    GRID_LOOP(B, nbf) {
+        const int a = face_tile(dim, elems, bowner, B, T);
+        key[B] = (uint64_t)a;
+        val[B] = (uint32_t)B;
+        atomicAdd(&tile_cnt[a], 1);
+        int h = 0;
+        for (int i = 0; i < dim; i++) h += (bface[dim * B + i] / T != a);
+        hb[B] = h;
+    }
+}
+
+__global__ void k_s_face_halo(int dim, int64_t nbf, const int32_t* elems, const int32_t* bface, const int32_t* bowner,
+                              const int32_t* bnode, int64_t nbn, int T, int bb, const int64_t* hoff, uint64_t* hk,
+                              uint32_t* hv) {
+    GRID_LOOP(B, nbf) {
+        const uint64_t a = (uint64_t)face_tile(dim, elems, bowner, B, T);
+        int64_t o = hoff[B];
+        for (int i = 0; i < dim; i++) {
+            const int v = bface[dim * B + i];
+            if (v / T != (int)a) {
+                hk[o] = (a << bb) | (uint64_t)lower_bound<int32_t>(bnode, nbn, v);
+                hv[o] = 0;
+                o++;
+            }
+        }
+    }
+}
+
+// merge pairs: (target, record index) with the record index = position in the
+// tile-major halo list
+__global__ void k_s_merge_pairs(const int32_t* list, int64_t n, uint64_t* key, uint32_t* val) {
+    GRID_LOOP(i, n) {
+        key[i] = (uint64_t)(uint32_t)list[i];
+        val[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_s_u64_low32(const uint64_t* k, int64_t n, int32_t* out) {
+    GRID_LOOP(i, n) out[i] = (int32_t)(uint32_t)k[i];
+}
+
+__global__ void k_s_tile_info(int64_t n_tiles, int T, int64_t nv, const int32_t* edges, int64_t n_edges,
+                              const int32_t* bnode, int64_t nbn, const int64_t* el_off, const int64_t* halo_off,
+                              const int64_t* hedge_off, const int64_t* hbo_off, const int64_t* bf_off, STile* tiles,
+                              int64_t* maxv, unsigned long long* status) {
+    GRID_LOOP(t, n_tiles) {
+        STile ti;
+        const int64_t n0 = t * T, n1 = n0 + T < nv ? n0 + T : nv;
+        const int64_t e0 = edge_lower_bound(edges, n_edges, (int32_t)n0);
+        const int64_t e1 = edge_lower_bound(edges, n_edges, (int32_t)n1);
+        const int64_t b0 = nbn ? lower_bound<int32_t>(bnode, nbn, (int32_t)n0) : 0;
+        const int64_t b1 = nbn ? lower_bound<int32_t>(bnode, nbn, (int32_t)n1) : 0;
+        ti.node0 = (int32_t)n0; ti.n_own = (int32_t)(n1 - n0);
+        ti.edge0 = (int32_t)e0; ti.n_eo = (int32_t)(e1 - e0);
+        ti.bnode0 = (int32_t)b0; ti.n_bo = (int32_t)(b1 - b0);
+        ti.n_halo = (int32_t)(halo_off[t + 1] - halo_off[t]);
+        ti.n_hedge = (int32_t)(hedge_off[t + 1] - hedge_off[t]);
+        ti.n_hbo = (int32_t)(hbo_off[t + 1] - hbo_off[t]);
+        ti.elem_off = (int32_t)el_off[t]; ti.n_el = (int32_t)(el_off[t + 1] - el_off[t]);
+        ti.halo_off = (int32_t)halo_off[t]; ti.hedge_off = (int32_t)hedge_off[t]; ti.hbo_off = (int32_t)hbo_off[t];
+        ti.bf_off = (int32_t)bf_off[t]; ti.n_bf = (int32_t)(bf_off[t + 1] - bf_off[t]);
+        tiles[t] = ti;
+        const int64_t ln = int64_t(ti.n_own) + ti.n_halo, le = int64_t(ti.n_eo) + ti.n_hedge,
+                      lb = int64_t(ti.n_bo) + ti.n_hbo;
+        if (ln > 65535 || le > 65535 || lb > 65535) atomicAdd(status, 1ull);
+        atomicMax((unsigned long long*)&maxv[0], (unsigned long long)ti.n_el);
+        atomicMax((unsigned long long*)&maxv[1], (unsigned long long)ln);
+        atomicMax((unsigned long long*)&maxv[2], (unsigned long long)le);
+        atomicMax((unsigned long long*)&maxv[3], (unsigned long long)lb);
+        atomicMax((unsigned long long*)&maxv[4], (unsigned long long)ti.n_bf);
+    }
+}
+
+__device__ __forceinline__ int s_local_node(const STile& ti, const int32_t* halo, int v) {
+    if (v >= ti.node0 && v < ti.node0 + ti.n_own) return v - ti.node0;
+    return ti.n_own + (int)lower_bound<int32_t>(halo + ti.halo_off, ti.n_halo, v);
+}
+
+__device__ __forceinline__ int s_local_edge(const STile& ti, const int32_t* hedge, int32_t e) {
+    if (e >= ti.edge0 && e < ti.edge0 + ti.n_eo) return e - ti.edge0;
+    return ti.n_eo + (int)lower_bound<int32_t>(hedge + ti.hedge_off, ti.n_hedge, e);
+}
+
+__device__ __forceinline__ int s_local_bnode(const STile& ti, const int32_t* hbo, int32_t b) {
+    if (b >= ti.bnode0 && b < ti.bnode0 + ti.n_bo) return b - ti.bnode0;
+    return ti.n_bo + (int)lower_bound<int32_t>(hbo + ti.hbo_off, ti.n_hbo, b);
+}
+
+// element records of the scatter tiles, at their sorted positions
+__global__ void k_s_elem_records(int dim, int64_t ne, const uint64_t* key, const uint32_t* val, const int32_t* elems,
+                                 const int32_t* e2e, const STile* tiles, const int32_t* halo, const int32_t* hedge,
+                                 ElemConn* conn, ElemEdges* tedge) {
+    const int nle = dim == 3 ? 6 : 3;
+    GRID_LOOP(i, ne) {
+        const STile ti = tiles[key[i] >> 5];
+        const int64_t E = val[i];
+        int v[4], pos[4];
+        sorted_nodes(dim, ld_el(elems, E), v, pos);
+        ElemConn c;
+        c.v[3] = 0xffff;
+        for (int r = 0; r <= dim; r++) c.v[r] = (uint16_t)s_local_node(ti, halo, v[r]);
+        conn[i] = c;
+        ElemEdges ed;
+        for (int q = 0; q < 8; q++) ed.e[q] = 0xffff;
+        for (int s2 = 0; s2 < nle; s2++) {
+            const int p = dim == 3 ? c_se3[s2][0] : c_se2[s2][0];
+            const int q = dim == 3 ? c_se3[s2][1] : c_se2[s2][1];
+            const int32_t e = e2e[E * nle + stored_edge(dim, pos[p], pos[q])];
+            ed.e[s2] = (uint16_t)s_local_edge(ti, hedge, e);
+        }
+        tedge[i] = ed;
+    }
+}
+
+__global__ void k_s_face_records(int dim, int64_t nbf, const uint64_t* key, const uint32_t* val, const int32_t* bface,
+                                 const int32_t* edges, int64_t n_edges, const int32_t* bnode, int64_t nbn,
+                                 const STile* tiles, const int32_t* halo, const int32_t* hedge, const int32_t* hbo,
+                                 SFace* sbf) {
+    GRID_LOOP(i, nbf) {
+        const STile ti = tiles[key[i]];
+        const int64_t B = val[i];
+        SFace r;
+        for (int q = 0; q < 3; q++) { r.v[q] = 0xffff; r.e[q] = 0xffff; r.b[q] = 0xffff; r.pad[q] = 0; }
+        for (int a = 0; a < dim; a++) {
+            const int v = bface[dim * B + a];
+            r.v[a] = (uint16_t)s_local_node(ti, halo, v);
+            r.b[a] = (uint16_t)s_local_bnode(ti, hbo, (int32_t)lower_bound<int32_t>(bnode, nbn, v));
+            if (dim == 3 || a == 0) {
+                const int w = bface[dim * B + (a + 1) % dim];
+                r.e[a] = (uint16_t)s_local_edge(ti, hedge, (int32_t)find_edge(edges, n_edges, v, w));
+            }
+        }
+        sbf[i] = r;
+    }
+}
+
+// merge CSR of sorted (target, record) pairs: heads -> unique targets and
+// their first pair
+__global__ void k_s_merge_csr(const uint64_t* k, const uint32_t* v, int64_t n, const int32_t* head, const int64_t* pos,
+                              int32_t* m_id, int32_t* m_ptr, int32_t* m_rec) {
+    GRID_LOOP(i, n) {
+        if (head[i]) {
+            m_id[pos[i]] = (int32_t)(uint32_t)k[i];
+            m_ptr[pos[i]] = (int32_t)i;
+        }
+        m_rec[i] = (int32_t)v[i];
+    }
+}
+
 #undef GRID_LOOP
 
 inline unsigned G(int64_t n) { return grid_for(n, NT); }
@@ -460,6 +672,242 @@ int csr_from_keys(uint64_t* keys, int64_t n, int64_t nkeys, int32_t* cnt, int64_
     EM_TRY(exclusive_scan_i32_to_i64(cnt, off64, nkeys, scan_ws, s));
     k_i64_to_i32<<<G(nkeys + 1), NT, 0, s>>>(off64, nkeys + 1, ptr);
     EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+// ---- scatter tiles: host side ---------------------------------------------------
+struct SCounts {
+    int64_t n_halo = 0, n_hedge = 0, n_hbo = 0, n_me = 0, n_mn = 0, n_mb = 0;
+};
+
+struct SOffsets {
+    int64_t tiles, conn, tedge, halo, hedge, hbo, sbf, me_id, me_ptr, me_rec, mn_id, mn_ptr, mn_rec, mb_id, mb_ptr,
+        mb_rec, total;
+};
+
+SOffsets s_offsets(int64_t base, int64_t n_tiles, int64_t ne, int64_t nbf, const SCounts& c) {
+    SOffsets o;
+    size_t p = (size_t)base;
+    auto take = [&](size_t bytes) { p = align256(p); int64_t r = (int64_t)p; p += bytes; return r; };
+    o.tiles = take(sizeof(STile) * n_tiles);
+    o.conn = take(sizeof(ElemConn) * ne);
+    o.tedge = take(sizeof(ElemEdges) * ne);
+    o.halo = take(4 * c.n_halo);
+    o.hedge = take(4 * c.n_hedge);
+    o.hbo = take(4 * c.n_hbo);
+    o.sbf = take(sizeof(SFace) * nbf);
+    o.me_id = take(4 * c.n_me);
+    o.me_ptr = take(4 * (c.n_me + 1));
+    o.me_rec = take(4 * c.n_hedge);
+    o.mn_id = take(4 * c.n_mn);
+    o.mn_ptr = take(4 * (c.n_mn + 1));
+    o.mn_rec = take(4 * c.n_halo);
+    o.mb_id = take(4 * c.n_mb);
+    o.mb_ptr = take(4 * (c.n_mb + 1));
+    o.mb_rec = take(4 * c.n_hbo);
+    o.total = (int64_t)align256(p);
+    return o;
+}
+
+// dedicated scratch of the scatter-tile build (candidate lists are bounded by
+// D halo nodes and 3 halo edges per element, D halo boundary nodes per face)
+struct SScratch {
+    uint64_t* pk; uint32_t* pv;          // element pairs [ne]
+    int32_t *hn, *he;                    // candidate counts [ne]
+    int64_t *hoff, *heoff;               // [ne + 1]
+    uint64_t* ck; uint32_t* cv;          // candidates / merge pairs [cmax]
+    int32_t* head; int64_t* pos;         // [cmax], [cmax + 1]
+    int32_t* list;                       // unique list (count mode) [cmax]
+    uint64_t* fk; uint32_t* fv;          // face pairs [nbf]
+    int32_t* fh; int64_t* fhoff;         // [nbf], [nbf + 1]
+    int32_t *ecnt, *hcnt, *hecnt, *hbcnt, *fcnt;   // [n_tiles + 1]
+    int64_t *el_off, *halo_off, *hedge_off, *hbo_off, *bf_off;
+    int64_t* maxv;                        // [8]
+    unsigned long long* status;           // [2]
+};
+
+int64_t s_cmax(int dim, int64_t ne, int64_t nbf) {
+    return std::max<int64_t>({int64_t(dim) * ne, 3 * ne, int64_t(dim) * nbf, 1});
+}
+
+void s_take(WsLayout& L, SScratch& S, int dim, int64_t ne, int64_t nbf, int64_t n_tiles) {
+    const int64_t cm = s_cmax(dim, ne, nbf);
+    S.pk = L.take<uint64_t>(ne); S.pv = L.take<uint32_t>(ne);
+    S.hn = L.take<int32_t>(ne); S.he = L.take<int32_t>(ne);
+    S.hoff = L.take<int64_t>(ne + 1); S.heoff = L.take<int64_t>(ne + 1);
+    S.ck = L.take<uint64_t>(cm); S.cv = L.take<uint32_t>(cm);
+    S.head = L.take<int32_t>(cm); S.pos = L.take<int64_t>(cm + 1);
+    S.list = L.take<int32_t>(cm);
+    S.fk = L.take<uint64_t>(nbf + 1); S.fv = L.take<uint32_t>(nbf + 1);
+    S.fh = L.take<int32_t>(nbf + 1); S.fhoff = L.take<int64_t>(nbf + 1);
+    S.ecnt = L.take<int32_t>(n_tiles + 1); S.hcnt = L.take<int32_t>(n_tiles + 1);
+    S.hecnt = L.take<int32_t>(n_tiles + 1); S.hbcnt = L.take<int32_t>(n_tiles + 1);
+    S.fcnt = L.take<int32_t>(n_tiles + 1);
+    S.el_off = L.take<int64_t>(n_tiles + 1); S.halo_off = L.take<int64_t>(n_tiles + 1);
+    S.hedge_off = L.take<int64_t>(n_tiles + 1); S.hbo_off = L.take<int64_t>(n_tiles + 1);
+    S.bf_off = L.take<int64_t>(n_tiles + 1);
+    S.maxv = L.take<int64_t>(8);
+    S.status = L.take<unsigned long long>(2);
+}
+
+// sorted candidates -> unique list (out) and per-tile counts; returns the
+// number of unique entries through *n_out (synchronizes)
+int s_unique(uint64_t* k, int64_t n, int bits, SScratch& S, int32_t* out, int32_t* tile_cnt, int64_t n_tiles,
+             void* scan_ws, int64_t* n_out, cudaStream_t s) {
+    EM_CUDA_TRY(cudaMemsetAsync(tile_cnt, 0, 4 * (n_tiles + 1), s));
+    *n_out = 0;
+    if (n) {
+        k_heads64<<<G(n), NT, 0, s>>>(k, n, S.head);
+        EM_TRY(exclusive_scan_i32_to_i64(S.head, S.pos, n, scan_ws, s));
+        k_compact_unique<<<G(n), NT, 0, s>>>(k, n, bits, S.head, S.pos, out, tile_cnt);
+        EM_CUDA_TRY(cudaMemcpyAsync(n_out, S.pos + n, 8, cudaMemcpyDeviceToHost, s));
+    }
+    EM_CUDA_TRY(cudaStreamSynchronize(s));
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+// merge CSR of one halo list: (target, position) pairs sorted by target;
+// count mode (m_id == NULL) only counts the targets
+int s_merge(const int32_t* list, int64_t n, int bits, SScratch& S, uint64_t* kt, uint32_t* vt, void* sort_ws,
+            void* scan_ws, int32_t* m_id, int32_t* m_ptr, int32_t* m_rec, int64_t* n_targets, cudaStream_t s) {
+    *n_targets = 0;
+    if (n == 0) {
+        if (m_ptr) EM_CUDA_TRY(cudaMemsetAsync(m_ptr, 0, 4, s));
+        return EM_OK;
+    }
+    k_s_merge_pairs<<<G(n), NT, 0, s>>>(list, n, S.ck, S.cv);
+    EM_TRY(radix_sort_pairs(S.ck, S.cv, kt, vt, n, bits, sort_ws, s));
+    k_heads64<<<G(n), NT, 0, s>>>(S.ck, n, S.head);
+    EM_TRY(exclusive_scan_i32_to_i64(S.head, S.pos, n, scan_ws, s));
+    EM_CUDA_TRY(cudaMemcpyAsync(n_targets, S.pos + n, 8, cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (m_id) {
+        k_s_merge_csr<<<G(n), NT, 0, s>>>(S.ck, S.cv, n, S.head, S.pos, m_id, m_ptr, m_rec);
+        const int32_t tail = (int32_t)n;
+        EM_CUDA_TRY(cudaMemcpyAsync(m_ptr + *n_targets, &tail, 4, cudaMemcpyHostToDevice, s));
+        EM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+struct SInput {
+    int dim, T;
+    int64_t nv, ne, n_edges, nbf, nbn, n_tiles;
+    const int32_t *elems, *e2e, *edges, *bface, *bowner, *bnode;
+};
+
+// Scatter tiles.  plan == NULL: counts only (*c written).  Otherwise builds
+// every scatter section at the offsets *o (from the counts of a first call,
+// which this call reproduces) and fills the scatter fields of *h.
+int s_build(const SInput& in, SScratch& S, uint64_t* kt, uint32_t* vt, void* sort_ws, void* scan_ws, char* plan,
+            const SOffsets* o, SCounts* c, PlanHeader* h, cudaStream_t s) {
+    const int dim = in.dim, T = in.T;
+    const int64_t ne = in.ne, nbf = in.nbf, n_tiles = in.n_tiles;
+    const int bt = bits_for(std::max<int64_t>(n_tiles - 1, 1));
+    const int bn = bits_for(in.nv - 1), be = bits_for(in.n_edges - 1), bb = bits_for(std::max<int64_t>(in.nbn - 1, 1));
+    if (bt + 5 > 63 || bt + bn > 63 || bt + be > 63 || bt + bb > 63)
+        return fail(EM_ERR_ARG, "grid too large for the tile keys");
+    const bool build = plan != nullptr;
+    auto at = [&](int64_t off) { return reinterpret_cast<int32_t*>(plan + off); };
+    SCounts cc;
+
+    // elements: pairs sorted by (tile, residue) and halo candidate counts
+    EM_CUDA_TRY(cudaMemsetAsync(S.ecnt, 0, 4 * (n_tiles + 1), s));
+    k_s_pairs<<<G(ne), NT, 0, s>>>(dim, ne, in.elems, in.e2e, in.edges, T, S.pk, S.pv, S.ecnt, S.hn, S.he);
+    EM_TRY(radix_sort_pairs(S.pk, S.pv, kt, vt, ne, bt + 5, sort_ws, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.ecnt, S.el_off, n_tiles, scan_ws, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.hn, S.hoff, ne, scan_ws, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.he, S.heoff, ne, scan_ws, s));
+    int64_t HC = 0, HEC = 0;
+    EM_CUDA_TRY(cudaMemcpyAsync(&HC, S.hoff + ne, 8, cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaMemcpyAsync(&HEC, S.heoff + ne, 8, cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaStreamSynchronize(s));
+
+    // halo nodes: candidates (tile, node) -> sorted unique list per tile, then
+    // their merge lists; the same for halo edges and halo boundary nodes (one
+    // candidate buffer, used in turn)
+    int32_t* halo = build ? at(o->halo) : S.list;
+    if (HC) {
+        k_s_halo<<<G(ne), NT, 0, s>>>(dim, ne, in.elems, in.e2e, in.edges, T, bn, be, S.hoff, S.heoff, S.ck, S.cv,
+                                       nullptr, nullptr);
+        EM_TRY(radix_sort_pairs(S.ck, S.cv, kt, vt, HC, bt + bn, sort_ws, s));
+    }
+    EM_TRY(s_unique(S.ck, HC, bn, S, halo, S.hcnt, n_tiles, scan_ws, &cc.n_halo, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.hcnt, S.halo_off, n_tiles, scan_ws, s));
+    EM_TRY(s_merge(halo, cc.n_halo, bn, S, kt, vt, sort_ws, scan_ws, build ? at(o->mn_id) : nullptr,
+                   build ? at(o->mn_ptr) : nullptr, build ? at(o->mn_rec) : nullptr, &cc.n_mn, s));
+
+    int32_t* hedge = build ? at(o->hedge) : S.list;
+    if (HEC) {
+        k_s_halo<<<G(ne), NT, 0, s>>>(dim, ne, in.elems, in.e2e, in.edges, T, bn, be, S.hoff, S.heoff, nullptr, nullptr,
+                                       S.ck, S.cv);
+        EM_TRY(radix_sort_pairs(S.ck, S.cv, kt, vt, HEC, bt + be, sort_ws, s));
+    }
+    EM_TRY(s_unique(S.ck, HEC, be, S, hedge, S.hecnt, n_tiles, scan_ws, &cc.n_hedge, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.hecnt, S.hedge_off, n_tiles, scan_ws, s));
+    EM_TRY(s_merge(hedge, cc.n_hedge, be, S, kt, vt, sort_ws, scan_ws, build ? at(o->me_id) : nullptr,
+                   build ? at(o->me_ptr) : nullptr, build ? at(o->me_rec) : nullptr, &cc.n_me, s));
+
+    // boundary faces: tile of the owner element, stable by face id
+    EM_CUDA_TRY(cudaMemsetAsync(S.fcnt, 0, 4 * (n_tiles + 1), s));
+    int64_t HBC = 0;
+    if (nbf) {
+        k_s_faces<<<G(nbf), NT, 0, s>>>(dim, nbf, in.elems, in.bface, in.bowner, T, S.fk, S.fv, S.fcnt, S.fh);
+        EM_TRY(radix_sort_pairs(S.fk, S.fv, kt, vt, nbf, bt, sort_ws, s));
+        EM_TRY(exclusive_scan_i32_to_i64(S.fh, S.fhoff, nbf, scan_ws, s));
+        EM_CUDA_TRY(cudaMemcpyAsync(&HBC, S.fhoff + nbf, 8, cudaMemcpyDeviceToHost, s));
+        EM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    EM_TRY(exclusive_scan_i32_to_i64(S.fcnt, S.bf_off, n_tiles, scan_ws, s));
+    int32_t* hbo = build ? at(o->hbo) : S.list;
+    if (HBC) {
+        k_s_face_halo<<<G(nbf), NT, 0, s>>>(dim, nbf, in.elems, in.bface, in.bowner, in.bnode, in.nbn, T, bb, S.fhoff,
+                                             S.ck, S.cv);
+        EM_TRY(radix_sort_pairs(S.ck, S.cv, kt, vt, HBC, bt + bb, sort_ws, s));
+    }
+    EM_TRY(s_unique(S.ck, HBC, bb, S, hbo, S.hbcnt, n_tiles, scan_ws, &cc.n_hbo, s));
+    EM_TRY(exclusive_scan_i32_to_i64(S.hbcnt, S.hbo_off, n_tiles, scan_ws, s));
+    EM_TRY(s_merge(hbo, cc.n_hbo, bb, S, kt, vt, sort_ws, scan_ws, build ? at(o->mb_id) : nullptr,
+                   build ? at(o->mb_ptr) : nullptr, build ? at(o->mb_rec) : nullptr, &cc.n_mb, s));
+    if (!build) {
+        *c = cc;
+        return EM_OK;
+    }
+    if (cc.n_halo != c->n_halo || cc.n_hedge != c->n_hedge || cc.n_hbo != c->n_hbo || cc.n_me != c->n_me ||
+        cc.n_mn != c->n_mn || cc.n_mb != c->n_mb)
+        return fail(EM_ERR_CUDA, "scatter plan: counts differ between the sizing and the build pass");
+
+    // tile table, element records, face records
+    STile* tiles = reinterpret_cast<STile*>(plan + o->tiles);
+    EM_CUDA_TRY(cudaMemsetAsync(S.maxv, 0, 64, s));
+    EM_CUDA_TRY(cudaMemsetAsync(S.status, 0, 16, s));
+    k_s_tile_info<<<G(n_tiles), NT, 0, s>>>(n_tiles, T, in.nv, in.edges, in.n_edges, in.bnode, in.nbn, S.el_off,
+                                             S.halo_off, S.hedge_off, S.hbo_off, S.bf_off, tiles, S.maxv, S.status);
+    k_s_elem_records<<<G(ne), NT, 0, s>>>(dim, ne, S.pk, S.pv, in.elems, in.e2e, tiles, halo, hedge,
+                                           reinterpret_cast<ElemConn*>(plan + o->conn),
+                                           reinterpret_cast<ElemEdges*>(plan + o->tedge));
+    if (nbf)
+        k_s_face_records<<<G(nbf), NT, 0, s>>>(dim, nbf, S.fk, S.fv, in.bface, in.edges, in.n_edges, in.bnode, in.nbn,
+                                                tiles, halo, hedge, hbo, reinterpret_cast<SFace*>(plan + o->sbf));
+    EM_CUDA_TRY(cudaGetLastError());
+    int64_t mx[8];
+    unsigned long long st[2];
+    EM_CUDA_TRY(cudaMemcpyAsync(mx, S.maxv, sizeof(mx), cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaMemcpyAsync(st, S.status, sizeof(st), cudaMemcpyDeviceToHost, s));
+    EM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[0])
+        return fail(EM_ERR_ARG, std::to_string(st[0]) + " scatter tile(s) exceed the 16-bit local index limits: use a "
+                                                         "smaller tile_nodes");
+    h->s_max_el = mx[0]; h->s_max_nodes = mx[1]; h->s_max_edges = mx[2]; h->s_max_bnodes = mx[3]; h->s_max_bf = mx[4];
+    h->n_shalo = cc.n_halo; h->n_shedge = cc.n_hedge; h->n_shbo = cc.n_hbo;
+    h->n_me = cc.n_me; h->n_mn = cc.n_mn; h->n_mb = cc.n_mb;
+    h->off_stiles = o->tiles; h->off_sconn = o->conn; h->off_stedge = o->tedge; h->off_shalo = o->halo;
+    h->off_shedge = o->hedge; h->off_shbo = o->hbo; h->off_sbf = o->sbf;
+    h->off_me_id = o->me_id; h->off_me_ptr = o->me_ptr; h->off_me_rec = o->me_rec;
+    h->off_mn_id = o->mn_id; h->off_mn_ptr = o->mn_ptr; h->off_mn_rec = o->mn_rec;
+    h->off_mb_id = o->mb_id; h->off_mb_ptr = o->mb_ptr; h->off_mb_rec = o->mb_rec;
     return EM_OK;
 }
 
@@ -562,7 +1010,10 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     int64_t* maxv = L.take<int64_t>(8);
     int64_t* smax = L.take<int64_t>(4);
     unsigned long long* status = L.take<unsigned long long>(2);
+    SScratch S;
+    s_take(L, S, dim, ne, nbf, n_tiles);
     const size_t full_bytes = L.bytes();
+    const SInput sin{dim, T, nv, ne, n_edges, nbf, nbn, n_tiles, elems, e2e, edges, bface, bowner, bnode};
 
     const int bt = bits_for(std::max<int64_t>(n_tiles - 1, 1));
     const int bn = bits_for(nv - 1);
@@ -573,7 +1024,10 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
         if (plan) return fail(EM_ERR_WORKSPACE, "plan workspace too small: need " + std::to_string(full_bytes));
         // size report with halo counts bounded by their candidates
         PlanOffsets po = plan_offsets(n_tiles, nv, n_edges, nbn, P, HC, HEC, ES, NS, BP, BS);
-        *plan_bytes = (size_t)po.total;
+        SCounts sb;
+        sb.n_halo = dim * ne; sb.n_hedge = 3 * ne; sb.n_hbo = dim * nbf;
+        sb.n_me = n_edges; sb.n_mn = nv; sb.n_mb = nbn;
+        *plan_bytes = (size_t)s_offsets(po.total, n_tiles, ne, nbf, sb).total;
         *ws_bytes = full_bytes;
         return EM_OK;
     }
@@ -612,13 +1066,17 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     EM_CUDA_TRY(cudaGetLastError());
 
     PlanOffsets po = plan_offsets(n_tiles, nv, n_edges, nbn, P, n_halo, n_hedge, ES, NS, BP, BS);
+    // scatter tiles: exact counts, then the sections behind the gather plan
+    SCounts sc;
+    EM_TRY(s_build(sin, S, kt, vt, sort_ws, scan_b, nullptr, nullptr, &sc, nullptr, s));
+    const SOffsets so = s_offsets(po.total, n_tiles, ne, nbf, sc);
     if (!plan) {
-        *plan_bytes = (size_t)po.total;
+        *plan_bytes = (size_t)so.total;
         *ws_bytes = full_bytes;
         return EM_OK;
     }
-    if (*plan_bytes < (size_t)po.total)
-        return fail(EM_ERR_WORKSPACE, "plan buffer too small: need " + std::to_string(po.total));
+    if (*plan_bytes < (size_t)so.total)
+        return fail(EM_ERR_WORKSPACE, "plan buffer too small: need " + std::to_string(so.total));
     char* pb = static_cast<char*>(plan);
     TileInfo* tiles = reinterpret_cast<TileInfo*>(pb + po.tiles);
     ElemConn* conn = reinterpret_cast<ElemConn*>(pb + po.conn);
@@ -709,9 +1167,10 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
     h.off_tiles = po.tiles; h.off_conn = po.conn; h.off_tedge = po.tedge; h.off_halo = po.halo; h.off_hedge = po.hedge;
     h.off_eslot_ptr = po.eslot_ptr; h.off_eslot = po.eslot; h.off_nslot_ptr = po.nslot_ptr; h.off_nslot = po.nslot;
     h.off_tbf = po.tbf; h.off_bslot_ptr = po.bslot_ptr; h.off_bslot = po.bslot;
+    EM_TRY(s_build(sin, S, kt, vt, sort_ws, scan_b, pb, &so, &sc, &h, s));
     EM_CUDA_TRY(cudaMemcpyAsync(plan, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     EM_CUDA_TRY(cudaStreamSynchronize(s));
-    *plan_bytes = (size_t)po.total;
+    *plan_bytes = (size_t)so.total;
     if (plan_info) {
         for (int i = 0; i < EM_PLAN_INFO_LEN; i++) plan_info[i] = 0;
         plan_info[EM_PLAN_INFO_TILE_NODES] = T;
@@ -723,7 +1182,15 @@ int plan_build_impl(int dim, int64_t nv, int64_t ne, const int32_t* elems, const
         plan_info[EM_PLAN_INFO_MAX_BFACES] = h.max_bf;
         plan_info[EM_PLAN_INFO_MAX_OWNED_BNODES] = h.max_bo;
         plan_info[EM_PLAN_INFO_MAX_OWNED_NODES] = h.max_own;
-        plan_info[EM_PLAN_INFO_CHECK] = po.total;
+        plan_info[EM_PLAN_INFO_CHECK] = so.total;
+        plan_info[EM_PLAN_INFO_S_MAX_ELEMS] = h.s_max_el;
+        plan_info[EM_PLAN_INFO_S_MAX_NODES] = h.s_max_nodes;
+        plan_info[EM_PLAN_INFO_S_MAX_EDGES] = h.s_max_edges;
+        plan_info[EM_PLAN_INFO_S_MAX_BNODES] = h.s_max_bnodes;
+        plan_info[EM_PLAN_INFO_S_MAX_BFACES] = h.s_max_bf;
+        plan_info[EM_PLAN_INFO_REC_NODES] = h.n_shalo;
+        plan_info[EM_PLAN_INFO_REC_EDGES] = h.n_shedge;
+        plan_info[EM_PLAN_INFO_REC_BNODES] = h.n_shbo;
         plan_info[EM_PLAN_INFO_MAX_ESLOTS] = sm[0];
         plan_info[EM_PLAN_INFO_MAX_NSLOTS] = sm[1];
         plan_info[EM_PLAN_INFO_MAX_BSLOTS] = sm[2];

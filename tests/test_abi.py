@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_error_paths(lib):
     import paper_2502_00778_gb300 as p
     L = p.load()
-    assert L.em_version() == 100
+    assert L.em_version() == 200
     # NULL mesh -> EM_ERR_ARG, no device work
     st = L.em_edge_metrics(None, 0, 0, None, None, None, None, None, None, None)
     assert st == -1
@@ -95,7 +95,7 @@ def test_newer_entry_points_reject_bad_arguments(lib):
     L.em_last_error(buf, 256)
     assert b"boundary-normal" in buf.value      # weights are refused on the ordered-gather path
     big = ctypes.c_size_t(1 << 20)
-    info = (ctypes.c_int64 * 16)()
+    info = (ctypes.c_int64 * p._lib.PLAN_INFO_LEN)()
     st = L.em_batched_fwd_adj(0, None, None, 1, info, 3, 1, 0, None, fake, ctypes.byref(big), None)
     assert st == -1
     st = L.em_batched_fwd_adj(1, fake, fake, 0, info, 3, 1, 0, fake, fake, ctypes.byref(big), None)
