@@ -329,8 +329,13 @@ int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* 
 /* ------------------------------------------------------------------------ */
 
 /* Size of the fixed scratch array behind em_edge_metrics_noalloc: 64 MiB of
- * device memory that every GPU which loads this library keeps reserved until
- * the process exits. */
+ * device memory that every GPU which loads this library's kernels keeps
+ * reserved until the process exits.  With lazy module loading (the CUDA
+ * default since 12.2) the array is committed when the module that holds it
+ * is first loaded on a device: at the first em_edge_metrics_noalloc call
+ * there (the address lookup), or at the first ATOMIC-path call of any entry
+ * point.  Processes under a fixed memory cap should make one such call
+ * during set-up; later calls commit nothing more. */
 #define EM_NOALLOC_SCRATCH_BYTES (64ull * 1024ull * 1024ull)
 
 /* em_edge_metrics_noalloc -- the forward outputs (n_edge, vol, bnormal, as
@@ -348,8 +353,9 @@ int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* 
  * 4 * (2*dim*n_edges + 2*n_nodes) <= EM_NOALLOC_SCRATCH_BYTES, otherwise
  * EM_ERR_ARG and nothing is enqueued.
  *   - The first call on each device looks up the array's device address
- *     (once per device, with that device current); make that first call
- *     before any stream capture begins.
+ *     (once per device, with that device current), which loads the module
+ *     and commits the 64 MiB if no ATOMIC-path call did so before; make that
+ *     first call during set-up, before any stream capture begins.
  *   - The array is cleared on `stream` at the start of every call.  All calls
  *     share it, so calls whose work overlaps on the GPU (different streams or
  *     threads, same device) race and corrupt each other's results; serialize

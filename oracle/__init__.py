@@ -211,6 +211,50 @@ def adjoint(dim, x, elems, topo, w, c, bw=None):
     return g
 
 
+_lib_omp = None
+
+
+def lib_omp():
+    """The multi-core CPU baseline (oracle_omp.c): the oracle's element
+    arithmetic with its loops split over OpenMP threads.  A timing baseline,
+    not a parity reference (its summation order follows the thread
+    schedule)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            L = ctypes.CDLL(_build.build_omp())
+            L.or_fused_omp.restype = None
+            L.or_fused_omp.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _f64p, _i64, _i32p, _i32p, _i64, _i32p,
+                                       _i64, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+            L.or_omp_max_threads.restype = ctypes.c_int
+            L.or_omp_max_threads.argtypes = []
+            _lib_omp = L
+    return _lib_omp
+
+
+def fused_omp(dim, x, elems, topo, w, c, threads=0):
+    """Forward (n, V, bnormal) and dL/dx on `threads` cores (0: all the
+    OpenMP runtime offers); returns (n, V, bnormal, grad)."""
+    x = _c(x, np.float64)
+    elems = _c(elems, np.int32)
+    w = _c(w, np.float64)
+    c = _c(c, np.float64)
+    nv = x.shape[0]
+    n = np.empty((topo.n_edges, dim))
+    v = np.empty(nv)
+    bfull = np.empty((nv, dim))
+    g = np.empty((nv, dim))
+    lib_omp().or_fused_omp(int(threads), dim, nv, _p(x, _f64p), elems.shape[0], _p(elems, _i32p),
+                           _p(topo.elem2edge, _i32p), topo.n_edges, _p(topo.edges, _i32p), topo.bface.shape[0],
+                           _p(topo.bface, _i32p), _p(w, _f64p), _p(c, _f64p), _p(n, _f64p), _p(v, _f64p),
+                           _p(bfull, _f64p), _p(g, _f64p))
+    return n, v, bfull[topo.bnode.astype(np.int64)], g
+
+
+def omp_threads():
+    return int(lib_omp().or_omp_max_threads())
+
+
 def loss_subset(dim, x, elems, topo, sel, bsel, w, c, bw=None):
     x = _c(x, np.float64)
     elems = _c(elems, np.int32)

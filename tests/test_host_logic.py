@@ -101,3 +101,28 @@ def test_oracle_sample_is_self_contained():
     assert np.array_equal(used, np.arange(x.shape[0]))      # every sampled node used, ids dense
     assert np.array_equal(np.sort(m.x[np.unique(m.elems[:100, :4])], axis=0), np.sort(x, axis=0))
     assert w.shape == (topo.n_edges, 3) and c.shape == (x.shape[0],)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_multicore_baseline_computes_the_oracle_result(dim):
+    """The benchmark's all-cores CPU baseline (the oracle's element arithmetic
+    with its loops split over threads, atomic accumulation) gives the serial
+    oracle's forward and gradient up to summation order."""
+    try:
+        oracle.lib_omp()
+    except Exception as ex:  # gcc without OpenMP: the benchmark reports it unavailable
+        pytest.skip(f"oracle_omp not built: {ex}")
+    if dim == 3:
+        m = meshgen.kuhn_cube(9, jitter=0.25, seed=611, offset=1000.0)
+    else:
+        m = meshgen.tri_square(17, jitter=0.3, seed=612)
+    t = oracle.topology(dim, m.elems, m.x)
+    w, c = meshgen.generate.loss_weights(t.n_edges, m.n_nodes, dim)
+    rn, rv, rb = oracle.direct(dim, m.x, m.elems, t)
+    rg = oracle.adjoint(dim, m.x, m.elems, t, w, c)
+    for threads in (1, 4):
+        n, v, b, g = oracle.fused_omp(dim, m.x, m.elems, t, w, c, threads=threads)
+        assert np.abs(n - rn).max() <= 1e-12 * m.h ** (dim - 1)
+        assert np.abs(v - rv).max() <= 1e-12 * m.h ** dim
+        assert np.abs(b - rb).max() <= 1e-12 * m.h ** (dim - 1)
+        assert np.abs(g - rg).max() <= 1e-12 * np.abs(rg).max()

@@ -41,12 +41,21 @@ def test_noalloc_matches_workspace_form_on_two_calls(name):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     h = hscale(m)
     rn, rv, rb = oracle_fwd(name)
-    for _ in range(2):
-        n = torch.full_like(n0, float("nan"))
-        v = torch.full_like(v0, float("nan"))
-        b = torch.full_like(b0, float("nan"))
+    n = torch.empty_like(n0)
+    v = torch.empty_like(v0)
+    b = torch.empty_like(b0)
+    for call in range(2):
+        for t in (n, v, b):
+            t.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         check(L.em_edge_metrics_noalloc(ctypes.byref(ms), _p(x), _p(n), _p(v), _p(b), stream))
         torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:
+            # the first call may load the module (and commit its array); the
+            # second must not change the device's free memory at all
+            assert free1 == free0
         assert (n - n0).abs().max().item() <= TOL * h ** (m.dim - 1)
         assert (v - v0).abs().max().item() <= TOL * h ** m.dim
         assert (b - b0).abs().max().item() <= TOL * h ** (m.dim - 1)
