@@ -46,7 +46,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the per-form comparison timings")
     p.add_argument("--cpu-sample-elems", type=int, default=1_500_000)
-    p.add_argument("--cpu-reps", type=int, default=4)
+    p.add_argument("--cpu-reps", type=int, default=10)
+    p.add_argument("--cpu-omp-elems", type=int, default=6_000_000,
+                   help="sample of the multi-core CPU baseline (the first N Morton-ordered elements)")
     return p.parse_args()
 
 
@@ -188,6 +190,80 @@ def oracle_time(m, n_elems, reps):
     return el.shape[0] * reps / dt, dt, el.shape[0]
 
 
+def cpu_comparisons(m, args):
+    """The CPU comparison points beside the serial oracle baseline, all on the
+    host cores of this machine, each the mean of repeated runs like the
+    paper's timings (Sec. 5):
+      * the paper's comparison on one core: the traditional dual-face
+        construction (n_jk only, Sec. 3.1) against the proposed algorithm's
+        forward (n_jk, V_j and boundary normals), on the serial oracle;
+      * the proposed forward + adjoint on all cores (the oracle's element
+        arithmetic with its loops split over OpenMP threads).
+    Samples are contiguous Morton sub-grids: the oracle's own topology step
+    (qsort of every element edge and face) would take about a minute per
+    run on the full 160^3 grid."""
+    import oracle
+    out = {"host_cores": os.cpu_count()}
+    el, x, topo, w, c = oracle_sample(m, args.cpu_sample_elems)
+    ns = el.shape[0]
+    reps = args.cpu_reps
+
+    def mean_time(fn, k):
+        fn()   # warm (page-in)
+        ts = []
+        for _ in range(k):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return float(np.mean(ts))
+
+    t_trad = mean_time(lambda: oracle.traditional(m.dim, x, el, topo), reps)
+    t_dir = mean_time(lambda: oracle.direct(m.dim, x, el, topo), reps)
+    out["serial_traditional_vs_proposed"] = {
+        "sample_elements": ns, "runs": reps, "cores": 1,
+        "traditional_n_s": t_trad, "proposed_n_V_bnormal_s": t_dir,
+        "traditional_elements_per_s": ns / t_trad, "proposed_elements_per_s": ns / t_dir,
+        "speedup_proposed": t_trad / t_dir}
+    try:
+        th = oracle.omp_threads()
+        el2, x2, topo2, w2, c2 = oracle_sample(m, args.cpu_omp_elems)
+        n2 = el2.shape[0]
+        k = max(3, reps // 2)
+        t_omp = mean_time(lambda: oracle.fused_omp(m.dim, x2, el2, topo2, w2, c2, threads=th), k)
+        out["multicore_fwd_adj"] = {"value": n2 / t_omp, "unit": UNIT, "cores": th, "kind": "oracle_omp",
+                                    "sample_elements": n2, "runs": k, "s_per_run": t_omp}
+    except Exception as ex:  # no OpenMP in this host's compiler
+        out["multicore_fwd_adj"] = {"unavailable": str(ex)[:160]}
+    return out
+
+
+def fp64_ops(kernel):
+    """FP64 instructions per element of a native-FP64 kernel, counted by ncu
+    (thread-level DADD + DMUL + DFMA executed), from the committed summary,
+    if it was taken on the current source of that kernel."""
+    p = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        ent = json.load(open(p)).get(kernel)
+        if not ent:
+            return None
+        import hashlib
+        src = os.path.join(ROOT, ent["source"])
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != ent.get("source_sha1"):
+            return None
+        return float(ent["fp64_ops_per_element"])
+    except Exception:
+        return None
+
+
+def fp64_peak_ops():
+    """FP64 pipe peak, thread instructions per second: 2 FP64 lanes per SM
+    per clock (1/64 of the 128 FP32 lanes; the nominal 1.25 TFLOP/s FP64 rate
+    of a GB300 is 0.625 T FMA/s) x 152 SMs x the 2,070 MHz maximum SM clock."""
+    return 2 * 152 * 2.07e9
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -277,6 +353,63 @@ def batched_forms(api, dev, stream, n_meshes=64):
                      "speedup_vs_plain_fp64": base / ms_b, "per_grid_tiled_ms": round(ms_p, 4),
                      "tile_nodes": tile, "launch": "item grid" if blocks == 0 else "persistent",
                      "sweep_ms": sweep}
+    return out
+
+
+def small_configs(api, dev, stream):
+    """The 2D 16^2 latency case (per-call microseconds) and the 48^3 grid
+    (edge_build timed apart from the metrics; atomic, CSR and tiled paths)."""
+    import torch
+
+    def ev_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    for name, reps in (("tri16", 200), ("kuhn48", 20)):
+        mm = load_mesh(name)
+        x = torch.from_numpy(mm.x).to(dev)
+        el = torch.from_numpy(mm.elems).to(dev)
+        t0 = time.perf_counter()
+        topo = api.edge_build(el, x)
+        torch.cuda.synchronize()
+        eb = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            api.edge_build(el, x)
+            torch.cuda.synchronize()
+            eb.append((time.perf_counter() - t0) * 1e3)
+        t0 = time.perf_counter()
+        api.plan_build(topo, 256 if mm.dim == 3 else 128)
+        torch.cuda.synchronize()
+        pb = (time.perf_counter() - t0) * 1e3
+        g = torch.Generator(device="cpu").manual_seed(meshgen.SEED_BASE + 5)
+        w = torch.randn((topo.n_edges, mm.dim), generator=g, dtype=torch.float64).to(dev)
+        c = torch.randn(mm.n_nodes, generator=g, dtype=torch.float64).to(dev)
+        o = (torch.empty((topo.n_edges, mm.dim), dtype=torch.float64, device=dev),
+             torch.empty(mm.n_nodes, dtype=torch.float64, device=dev),
+             torch.empty((topo.n_bnodes, mm.dim), dtype=torch.float64, device=dev),
+             torch.empty((mm.n_nodes, mm.dim), dtype=torch.float64, device=dev))
+        r = {"elements": mm.n_elems, "edge_build_ms": float(np.mean(eb)), "plan_build_ms": pb,
+             "fwd_atomic_fp64_ms": ev_ms(lambda: api.edge_metrics(topo, x, "fp64", "atomic", out=o[:3]), reps),
+             "fwd_csr_fp64_ms": ev_ms(lambda: api.edge_metrics(topo, x, "fp64", "csr", out=o[:3]), reps),
+             "fwd_tiled_dw_ms": ev_ms(lambda: api.edge_metrics(topo, x, "dw", "tiled", out=o[:3]), reps),
+             "fused_tiled_dw_ms": ev_ms(lambda: api.edge_metrics_fused(topo, x, w, c, "dw", out=o, path="tiled"),
+                                        reps)}
+        if name == "tri16":
+            r = {k: (v * 1e3 if k.endswith("_ms") and not k.startswith(("edge", "plan")) else v)
+                 for k, v in r.items()}
+            r = {(k[:-3] + "_us" if k.endswith("_ms") and not k.startswith(("edge", "plan")) else k): v
+                 for k, v in r.items()}
+        out[name] = r
     return out
 
 
@@ -391,7 +524,7 @@ def run_ours(args):
     # dominant kernel: the fused gather kernel, or the forward element kernel
     if path in ("gather", "tiled"):
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
-        what, kname = "fused", f"{'k_tile_scatter' if path == 'tiled' else 'k_tile'}<3,{prec},fwd+adj>"
+        what, kname = "fused", f"{'k_stile' if path == 'tiled' else 'k_tile'}<3,{prec},fwd+adj>"
     else:
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
         what, kname = "fwd", f"k_fwd_atomic3<{prec}>"
@@ -536,6 +669,26 @@ def run_ours(args):
             except Exception as ex:  # a form that is not built reports why
                 forms[f"{pth}/{pr}"] = {"unavailable": str(ex)[:120]}
 
+    # ---- FP64 ALU ceiling of the native-FP64 forms ----
+    fp64_alu = {}
+    for key, kern in (("fwd:atomic/fp64", "k_fwd_atomic3<fp64>"), ("fwd:tiled/fp64", "k_stile<3,fp64,fwd>"),
+                      ("tiled/fp64", "k_stile<3,fp64,fwd+adj>")):
+        ops = fp64_ops(kern)
+        f = forms.get(key, {})
+        if ops and "ms_per_step" in f:
+            ach = ops * m.n_elems / (f["ms_per_step"] * 1e-3)
+            fp64_alu[key] = {"bound": "alu", "kernel": kern, "fp64_ops_per_element": ops, "achieved": ach,
+                             "peak": fp64_peak_ops(), "unit": "FP64 thread instructions/s",
+                             "frac": ach / fp64_peak_ops()}
+
+    # ---- the small configurations: 2D latency case and the 48^3 grid ----
+    small = {}
+    if not args.no_forms and rank == 0:
+        try:
+            small = small_configs(api, dev, stream)
+        except Exception as ex:  # reported, not fatal
+            small = {"unavailable": str(ex)[:200]}
+
     batched = None
     if not args.no_forms and rank == 0 and m.dim == 3:
         try:
@@ -544,11 +697,13 @@ def run_ours(args):
             batched = {"unavailable": str(ex)[:200]}
 
     cpu = None
+    cpu_more = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, dt, ns = oracle_time(m, args.cpu_sample_elems, args.cpu_reps)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {ns} Morton-ordered elements of {args.workload}, forward + adjoint, "
-                         f"{args.cpu_reps} repetitions ({dt:.1f} s)"}
+                         f"mean of {args.cpu_reps} runs ({dt:.1f} s)"}
+        cpu_more = cpu_comparisons(m, args)
 
     if rank == 0:
         line = {
@@ -575,6 +730,9 @@ def run_ours(args):
             "clocks": clk,
             "edge_build_ms": edge_build_ms, "plan_build_ms": plan_build_ms,
             "forms": forms,
+            "fp64_alu_roofline": fp64_alu,
+            "small_configs": small,
+            "cpu_comparisons": cpu_more,
             "batched": batched,
         }
         print(json.dumps(line), flush=True)

@@ -324,6 +324,28 @@ int em_edge_residual(const em_mesh* mesh, const double* F, const double* n_edge,
 int em_check_elements(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems,
                       const double* x, void* ws, size_t* ws_bytes, int64_t* counts, void* stream);
 
+/* em_edge_metrics_partial -- one rank's share of a grid split into
+ * contiguous element ranges (multi-GPU partition of one grid).  Writes the
+ * contributions of the elements [elem_begin, elem_end), and of the boundary
+ * faces whose owner element (bface_owner / 4) lies in that range, to the
+ * GLOBAL arrays: n_edge [n_edges][dim], vol [n_nodes], bnormal
+ * [n_bnodes][dim] (forward) and grad_x [n_nodes][dim] (adjoint of L = sum
+ * w.n + sum c V, c NULL: zero), each overwritten, zero where the range
+ * contributes nothing.  The metrics are sums of per-element terms (Eq.
+ * efficient_njk_formula_general_D, Sec. 4.2) and per-boundary-face terms
+ * (the correction and closure of Sec. 3.2.3), so summing the partial arrays
+ * of disjoint ranges that cover the grid (one all-reduce, or a reduce onto
+ * the owner of each entry) gives the full result up to rounding order.
+ * Element arithmetic as the ATOMIC path: precision EM_PREC_FP64 or
+ * EM_PREC_MIXED, global FP64 atomics (the last bits vary from run to run),
+ * no workspace.  Give the three forward outputs together or none of them;
+ * grad_x NULL skips the adjoint (w is then unused).
+ * Errors: EM_ERR_ARG (range outside [0, n_elems], bad precision, missing
+ * arrays), EM_ERR_CUDA. */
+int em_edge_metrics_partial(const em_mesh* mesh, int precision, int64_t elem_begin, int64_t elem_end,
+                            const double* x, const double* w, const double* c,
+                            double* n_edge, double* vol, double* bnormal, double* grad_x, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free forward                                                   */
 /* ------------------------------------------------------------------------ */

@@ -62,6 +62,8 @@ SIGNATURES = {
     "em_edge_metrics_fused": ([_c.POINTER(EmMesh), _c.c_int, _c.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                _szp, _vp], _c.c_int),
     "em_edge_metrics_noalloc": ([_c.POINTER(EmMesh), _vp, _vp, _vp, _vp, _vp], _c.c_int),
+    "em_edge_metrics_partial": ([_c.POINTER(EmMesh), _c.c_int, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                                _c.c_int),
     "em_edge_volume": ([_c.POINTER(EmMesh), _vp, _vp, _vp, _vp, _szp, _vp], _c.c_int),
     "em_edge_areas_traditional": ([_c.POINTER(EmMesh), _vp, _vp, _vp], _c.c_int),
     "em_edge_residual": ([_c.POINTER(EmMesh), _vp, _vp, _vp, _vp, _vp, _szp, _vp], _c.c_int),

@@ -250,6 +250,33 @@ def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", ou
     return n, v, b, g
 
 
+def edge_metrics_partial(topo: Topology, x, elem_range, w=None, c=None, precision: str = "fp64", forward=True):
+    """One rank's share of a grid split into element ranges: the
+    contributions of elements [lo, hi) (and of the boundary faces they own)
+    to the global n [Ne, dim], V [Nv], bnormal [Nbn, dim] and, when w is
+    given, dL/dx [Nv, dim].  Returns (n, V, bnormal, grad), None for what was
+    not asked for.  Summing the tuples of ranges that cover the grid gives the
+    full result up to rounding order (sharding.reduce_partials)."""
+    L = load()
+    _require_cuda(x, w, c)
+    lo, hi = (int(v) for v in elem_range)
+    x = x.contiguous().to(torch.float64)
+    w = w.contiguous().to(torch.float64) if w is not None else None
+    c = c.contiguous().to(torch.float64) if c is not None else None
+    dev = x.device
+    n = v = b = g = None
+    if forward:
+        n = torch.empty((topo.n_edges, topo.dim), dtype=torch.float64, device=dev)
+        v = torch.empty(topo.n_nodes, dtype=torch.float64, device=dev)
+        b = torch.empty((topo.n_bnodes, topo.dim), dtype=torch.float64, device=dev)
+    if w is not None:
+        g = torch.empty((topo.n_nodes, topo.dim), dtype=torch.float64, device=dev)
+    m, mr = _mesh_ref(topo)
+    check(L.em_edge_metrics_partial(mr, PREC[precision], lo, hi, _ptr(x), _ptr(w), _ptr(c), _ptr(n), _ptr(v),
+                                    _ptr(b), _ptr(g), _stream()))
+    return n, v, b, g
+
+
 def edge_volume(topo: Topology, x, n_edge):
     """Edge-based dual volume (Sec. 4.1) from lumped directed-area vectors."""
     L = load()

@@ -233,6 +233,25 @@ int em_edge_metrics_noalloc(const em_mesh* mesh, const double* x, double* n_edge
     return st == EM_OK ? ok() : st;
 }
 
+int em_edge_metrics_partial(const em_mesh* mesh, int precision, int64_t elem_begin, int64_t elem_end,
+                            const double* x, const double* w, const double* c, double* n_edge, double* vol,
+                            double* bnormal, double* grad_x, void* stream) {
+    EM_TRY(check_mesh(mesh));
+    if (precision != EM_PREC_FP64 && precision != EM_PREC_MIXED)
+        return fail(EM_ERR_ARG, "partial metrics support EM_PREC_FP64 and EM_PREC_MIXED");
+    if (elem_begin < 0 || elem_begin > elem_end || elem_end > mesh->n_elems)
+        return fail(EM_ERR_ARG, "element range must satisfy 0 <= elem_begin <= elem_end <= n_elems");
+    if (!x) return fail(EM_ERR_ARG, "x must not be NULL");
+    const bool fwd = n_edge || vol || bnormal;
+    if (fwd && (!n_edge || !vol || (mesh->n_bnodes && !bnormal)))
+        return fail(EM_ERR_ARG, "partial forward needs n_edge, vol and bnormal together");
+    if (grad_x && !w) return fail(EM_ERR_ARG, "partial adjoint needs w");
+    if (!fwd && !grad_x) return fail(EM_ERR_ARG, "nothing to compute: give the forward outputs, grad_x or both");
+    int st = atomic_partial(mesh, precision, elem_begin, elem_end, x, w, c, n_edge, vol, bnormal, grad_x,
+                            as_stream(stream));
+    return st == EM_OK ? ok() : st;
+}
+
 int em_plan_build(int dim, int64_t n_nodes, int64_t n_elems, const int32_t* elems, const int32_t* elem2edge,
                   int64_t n_edges, const int32_t* edges, int64_t n_bfaces, const int32_t* bface,
                   const int32_t* bface_owner, int64_t n_bnodes, const int32_t* bnode, int tile_nodes, void* ws,

@@ -246,16 +246,18 @@ __device__ __forceinline__ int64_t find_bnode(const int32_t* bnode, int64_t nb, 
     return -1;
 }
 
-// boundary faces: correction n_B/(D(D+1)) on the face's edges, n_B/D on its nodes
+// boundary faces: correction n_B/(D(D+1)) on the face's edges, n_B/D on its
+// nodes; only faces whose owner element lies in [e0, e1)
 template <int DIM>
 __global__ void k_bnd_atomic(int64_t nbf, const int32_t* __restrict__ bface, const int32_t* __restrict__ bowner,
                              const int32_t* __restrict__ elems, const int32_t* __restrict__ e2e,
                              const double* __restrict__ x, int64_t nbn, const int32_t* __restrict__ bnode,
-                             double* __restrict__ n, double* __restrict__ bnormal) {
+                             double* __restrict__ n, double* __restrict__ bnormal, int64_t e0, int64_t e1) {
     for (int64_t B = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; B < nbf; B += int64_t(gridDim.x) * blockDim.x) {
         int32_t f = bowner[B];
         int64_t E = f >> 2;
         int o = f & 3;
+        if (E < e0 || E >= e1) continue;
         if (DIM == 3) {
             int p = bface[3 * B], q = bface[3 * B + 1], r = bface[3 * B + 2];
             d3 xp = ld3(x, p);
@@ -385,14 +387,17 @@ __global__ void k_adj_atomic2(int64_t ne, const int32_t* __restrict__ elems, con
     }
 }
 
+// the boundary faces' part of the adjoint; only faces whose owner element
+// lies in [e0, e1)
 template <int DIM>
 __global__ void k_bnd_adj_atomic(int64_t nbf, const int32_t* __restrict__ bface, const int32_t* __restrict__ bowner,
                                  const int32_t* __restrict__ e2e, const double* __restrict__ x,
-                                 const double* __restrict__ w, double* __restrict__ g) {
+                                 const double* __restrict__ w, double* __restrict__ g, int64_t e0, int64_t e1) {
     for (int64_t B = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; B < nbf; B += int64_t(gridDim.x) * blockDim.x) {
         int32_t f = bowner[B];
         int64_t E = f >> 2;
         int o = f & 3;
+        if (E < e0 || E >= e1) continue;
         if (DIM == 3) {
             d3 WB = mk(0, 0, 0);
             for (int l = 0; l < 6; l++) {
@@ -565,10 +570,12 @@ int atomic_fwd(const em_mesh* m, int prec, const double* x, double* n, double* v
     if (m->n_bfaces && (n || bnormal)) {
         if (dim == 3)
             k_bnd_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
-                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal, 0,
+                                                                  INT64_MAX);
         else
             k_bnd_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
-                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal, 0,
+                                                                  INT64_MAX);
         note_launches(1);
     }
     EM_CUDA_TRY(cudaGetLastError());
@@ -592,11 +599,83 @@ int atomic_adj(const em_mesh* m, int prec, const double* x, const double* w, con
     if (m->n_bfaces) {
         if (dim == 3)
             k_bnd_adj_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
-                                                                      m->elem2edge, x, w, g);
+                                                                      m->elem2edge, x, w, g, 0, INT64_MAX);
         else
             k_bnd_adj_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
-                                                                      m->elem2edge, x, w, g);
+                                                                      m->elem2edge, x, w, g, 0, INT64_MAX);
         note_launches(1);
+    }
+    EM_CUDA_TRY(cudaGetLastError());
+    return EM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One contiguous range of elements [e0, e1) (a rank's part of a partitioned
+// grid): the contributions of its elements, and of the boundary faces whose
+// owner element lies in it, to the GLOBAL edge / node / boundary-node arrays.
+// Every metric is a sum of such per-element and per-face terms, so the sum of
+// the partial arrays of disjoint ranges covering the grid is the full result
+// up to rounding order.  FP64 or MIXED, global atomics, no workspace.
+// ---------------------------------------------------------------------------
+int atomic_partial(const em_mesh* m, int prec, int64_t e0, int64_t e1, const double* x, const double* w,
+                   const double* c, double* n, double* vol, double* bnormal, double* g, cudaStream_t s) {
+    const int T = 256;
+    const int dim = m->dim;
+    const int nle = dim == 3 ? 6 : 3;
+    const int64_t ne = e1 - e0;
+    const int32_t* el = m->elems + 4 * e0;        // 16-byte rows: stays 16-byte aligned
+    const int32_t* e2e = m->elem2edge + nle * e0;
+    const unsigned G = grid_for(ne > 0 ? ne : 1, T, int64_t(num_sms()) * 16);
+    const bool fp64 = prec == EM_PREC_FP64;
+    if (n || vol || bnormal) {
+        if (n) EM_CUDA_TRY(cudaMemsetAsync(n, 0, sizeof(double) * m->n_edges * dim, s));
+        if (vol) EM_CUDA_TRY(cudaMemsetAsync(vol, 0, sizeof(double) * m->n_nodes, s));
+        if (bnormal) EM_CUDA_TRY(cudaMemsetAsync(bnormal, 0, sizeof(double) * m->n_bnodes * dim, s));
+        if (ne > 0 && (n || vol)) {
+            double* nn = n;
+            if (!nn) return fail(EM_ERR_ARG, "partial forward: n_edge is required when vol is given");
+            if (dim == 3) {
+                if (fp64) k_fwd_atomic3<EM_PREC_FP64><<<G, T, 0, s>>>(ne, el, e2e, x, nn, vol, nullptr, nullptr, nullptr, nullptr);
+                else k_fwd_atomic3<EM_PREC_MIXED><<<G, T, 0, s>>>(ne, el, e2e, x, nn, vol, nullptr, nullptr, nullptr, nullptr);
+            } else {
+                if (fp64) k_fwd_atomic2<EM_PREC_FP64><<<G, T, 0, s>>>(ne, el, e2e, x, nn, vol, nullptr, nullptr, nullptr, nullptr);
+                else k_fwd_atomic2<EM_PREC_MIXED><<<G, T, 0, s>>>(ne, el, e2e, x, nn, vol, nullptr, nullptr, nullptr, nullptr);
+            }
+            note_launches(1);
+        }
+        if (m->n_bfaces && ne > 0 && (n || bnormal)) {
+            if (dim == 3)
+                k_bnd_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                      m->elem2edge, x, m->n_bnodes, m->bnode, n,
+                                                                      bnormal, e0, e1);
+            else
+                k_bnd_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
+                                                                      m->elem2edge, x, m->n_bnodes, m->bnode, n,
+                                                                      bnormal, e0, e1);
+            note_launches(1);
+        }
+    }
+    if (g) {
+        EM_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * m->n_nodes * dim, s));
+        if (ne > 0) {
+            if (dim == 3) {
+                if (fp64) k_adj_atomic3<EM_PREC_FP64><<<G, T, 0, s>>>(ne, el, e2e, x, w, c, g);
+                else k_adj_atomic3<EM_PREC_MIXED><<<G, T, 0, s>>>(ne, el, e2e, x, w, c, g);
+            } else {
+                if (fp64) k_adj_atomic2<EM_PREC_FP64><<<G, T, 0, s>>>(ne, el, e2e, x, w, c, g);
+                else k_adj_atomic2<EM_PREC_MIXED><<<G, T, 0, s>>>(ne, el, e2e, x, w, c, g);
+            }
+            note_launches(1);
+            if (m->n_bfaces) {
+                if (dim == 3)
+                    k_bnd_adj_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
+                                                                              m->elem2edge, x, w, g, e0, e1);
+                else
+                    k_bnd_adj_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner,
+                                                                              m->elem2edge, x, w, g, e0, e1);
+                note_launches(1);
+            }
+        }
     }
     EM_CUDA_TRY(cudaGetLastError());
     return EM_OK;
@@ -663,10 +742,12 @@ int atomic_fwd_noalloc(const em_mesh* m, const double* x, double* n, double* vol
     if (m->n_bfaces) {
         if (dim == 3)
             k_bnd_atomic<3><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
-                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal, 0,
+                                                                  INT64_MAX);
         else
             k_bnd_atomic<2><<<grid_for(m->n_bfaces, T), T, 0, s>>>(m->n_bfaces, m->bface, m->bface_owner, m->elems,
-                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal);
+                                                                  m->elem2edge, x, m->n_bnodes, m->bnode, n, bnormal, 0,
+                                                                  INT64_MAX);
         note_launches(1);
     }
     EM_CUDA_TRY(cudaGetLastError());

@@ -24,6 +24,8 @@ size_t atomic_fwd_ws_bytes(const em_mesh* m, int prec);
 int atomic_fwd(const em_mesh* m, int prec, const double* x, double* n, double* vol, double* bnormal, void* ws,
                cudaStream_t s);
 int atomic_fwd_noalloc(const em_mesh* m, const double* x, double* n, double* vol, double* bnormal, cudaStream_t s);
+int atomic_partial(const em_mesh* m, int prec, int64_t e0, int64_t e1, const double* x, const double* w,
+                   const double* c, double* n, double* vol, double* bnormal, double* g, cudaStream_t s);
 int atomic_adj(const em_mesh* m, int prec, const double* x, const double* w, const double* c, double* g,
                cudaStream_t s);
 

@@ -50,3 +50,42 @@ def owned_boundary_faces(bface_owner, lo, hi):
     import numpy as np
     e = np.asarray(bface_owner) // 4
     return np.nonzero((e >= lo) & (e < hi))[0]
+
+
+def reduce_partials(parts, group=None):
+    """Sum one rank's partial metric arrays (from api.edge_metrics_partial)
+    over all ranks of `group` in place: the one exchange step of a partitioned
+    grid.  Without an initialised process group (one process holding every
+    range) it returns the arrays unchanged.  None entries are skipped."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return parts
+    gloo = dist.get_backend(group) == "gloo"
+    for a in parts:
+        if a is None:
+            continue
+        if gloo and a.is_cuda:   # gloo reduces host copies
+            t = a.cpu()
+            dist.all_reduce(t, group=group)
+            a.copy_(t)
+        else:
+            dist.all_reduce(a, group=group)
+    return parts
+
+
+def partitioned_metrics(topo, x, w=None, c=None, precision="fp64", rank=None, world_size=None, group=None):
+    """The metrics of one grid computed by `world_size` ranks, each on its
+    contiguous element range (this rank's range through the CUDA kernels),
+    summed over the ranks: equals the single-rank result up to rounding
+    order.  rank / world_size default to the process group's."""
+    from . import api
+    import torch.distributed as dist
+    if rank is None or world_size is None:
+        if dist.is_available() and dist.is_initialized():
+            rank, world_size = dist.get_rank(group), dist.get_world_size(group)
+        else:
+            rank, world_size = 0, 1
+    lo, hi = element_ranges(topo.n_elems, world_size)[rank]
+    parts = api.edge_metrics_partial(topo, x, (lo, hi), w, c, precision)
+    return reduce_partials(parts, group)
+

@@ -106,3 +106,31 @@ def test_newer_entry_points_reject_bad_arguments(lib):
     assert st == -1                             # unknown launch shape
     L.em_last_error(buf, 256)
     assert b"blocks" in buf.value
+
+
+def test_partial_entry_point_rejects_bad_arguments(lib):
+    """em_edge_metrics_partial validates its range, precision and outputs
+    before any device work."""
+    import paper_2502_00778_gb300 as p
+    L = p.load()
+    buf = ctypes.create_string_buffer(256)
+    m = p._lib.EmMesh()
+    m.dim, m.n_nodes, m.n_elems, m.n_edges = 3, 4, 1, 6
+    m.elems = m.elem2edge = m.edges = 4096   # never dereferenced: validation fails first
+    fake = ctypes.c_void_p(4096)
+    null = None
+    # range outside [0, n_elems]
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 2, fake, null, null, fake, fake, fake, null, null) == -1
+    L.em_last_error(buf, 256)
+    assert b"range" in buf.value
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 1, 0, fake, null, null, fake, fake, fake, null, null) == -1
+    # forms other than FP64 and MIXED
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 1, 0, 1, fake, null, null, fake, fake, fake, null, null) == -1
+    L.em_last_error(buf, 256)
+    assert b"EM_PREC_FP64" in buf.value
+    # forward outputs only in part, adjoint without w, nothing asked
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 1, fake, null, null, fake, null, null, null, null) == -1
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 1, fake, null, null, null, null, null, fake, null) == -1
+    L.em_last_error(buf, 256)
+    assert b"needs w" in buf.value
+    assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 1, fake, null, null, null, null, null, null, null) == -1

@@ -103,7 +103,7 @@ def test_wide_tiles_equal_batched(prec, blocks):
     with torch.profiler.profile(activities=[torch.profiler.ProfilerActivity.CUDA]) as prof:
         refs = [api.edge_metrics_fused(t, x, w, c, prec, path="tiled") for t, x, w, c in zip(topos, xs, ws, cs)]
         torch.cuda.synchronize()
-    names = {e.name for e in prof.events() if "k_tile_scatter" in e.name}
+    names = {e.name for e in prof.events() if "k_stile" in e.name}
     for o, ref in zip(b.outs, refs):
         for a, r in zip(o, ref):
             assert torch.equal(a, r)
