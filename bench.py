@@ -464,6 +464,11 @@ def run_ours(args):
         tile = None
         if path in ("gather", "tiled", "auto"):
             path, prec = "atomic", "fp64"
+    plan_stats = None
+    if have_gather and getattr(topo, "plan_info", None):
+        pi = topo.plan_info
+        plan_stats = {"tiles": pi[1], "plan_bytes": int(topo.plan.numel()), "node_records": pi[20],
+                      "edge_records": pi[21], "bnode_records": pi[22]}
     outs = (torch.empty((topo.n_edges, m.dim), dtype=torch.float64, device=dev),
             torch.empty(m.n_nodes, dtype=torch.float64, device=dev),
             torch.empty((topo.n_bnodes, m.dim), dtype=torch.float64, device=dev),
@@ -715,7 +720,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "elements": m.n_elems, "nodes": m.n_nodes, "edges": topo.n_edges,
                        "path": path, "precision": prec, "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (no flush needed)", "tile_nodes": tile,
-                       "tile_sweep_ms": sweep},
+                       "tile_sweep_ms": sweep, "plan": plan_stats},
             "hbm_gbs_step": step_bytes / (ms_per_step * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kname,

@@ -42,7 +42,12 @@
 // W_1 = w12+w13, W_2 = w23, A_1 = W_1 - W_0, A_2 = W_2 - W_0, A_3 = -W_0 and
 // C = c0+c1+c2+c3, the gradient at node k (k = 1, 2, 3, indices cyclic,
 // X = (a, b, c)) is g_k = -s/12 (A_{k+1} x X_{k+2} - A_{k+2} x X_{k+1})
-// + s C/24 N_k, and at node 0 -(g_1 + g_2 + g_3).
+// + s C/24 N_k, and at node 0 -(g_1 + g_2 + g_3).  Since N_1 = b x c, etc.,
+// the volume term folds into the cross products: with A''_k = A_k - (C/4) X_k,
+// g_k = -s/12 (A''_{k+1} x X_{k+2} - A''_{k+2} x X_{k+1}).  The 3D tile sums
+// hold 12 g (the 1/12 is applied once per output), and node 0's share is the
+// integer sum -(q_1 + q_2 + q_3) of the other nodes' quantised values, as is
+// the share of the edges at node 0 in the forward (m0 = -(m1 + m2 + m3)).
 #include "em_common.cuh"
 #include "em_dw.cuh"
 #include "em_kernels.cuh"
@@ -349,8 +354,8 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
         // |w|, |c|, |bw| < 2^Ew, 2^Ec, 2^Eb
         const int Ew = key_exp(red_max(wred, 1, NW)), Ec = key_exp(red_max(wred, 2, NW));
         const int Eb = A.bwa.bw ? key_exp(*A.bwa.key) : -2000;
-        if (DIM == 3)   // (16 |w| Lx + 8 |c| Lx^2 + 16 |bw| Lx) 2 Kv
-            eg = max(max(4 + Ew + eL, 3 + Ec + 2 * eL), 4 + Eb + eL) + 2 + 1 + eKv;
+        if (DIM == 3)   // 12 (16 |w| Lx + 8 |c| Lx^2 + 16 |bw| Lx) 2 Kv: the 3D sums hold 12 g
+            eg = max(max(4 + Ew + eL, 3 + Ec + 2 * eL), 4 + Eb + eL) + 2 + 1 + eKv + 4;
         else            // (4 |w| + 4 |c| Lx + 4 |bw|) 2 Kv
             eg = max(max(2 + Ew, 2 + Ec + eL), 2 + Eb) + 2 + 1 + eKv;
     }
@@ -417,73 +422,63 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
             V det = F::add(F::add(F::mul(a[0], N1[0]), F::mul(a[1], N1[1])), F::mul(a[2], N1[2]));
             const float s = F::sign_of(det);
             if (WHAT & DO_FWD) {
-                // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2
+                // edges (0,1),(0,2),(0,3) <- m0; (1,2),(1,3) <- m1; (2,3) <- m2,
+                // m_k = -s N_k and m0 = -(m1 + m2 + m3), summed as integers
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const Lq q0 = FX::q(F::sgn(F::add(F::add(N1[d], N2[d]), N3[d]), s), sg_e);
+                    const Lq q1 = FX::q(F::sgn(N1[d], -s), sg_e);
+                    const Lq q2 = FX::q(F::sgn(N2[d], -s), sg_e);
+                    const Lq q0 = lq_neg_sum(q1, q2, FX::q(F::sgn(N3[d], -s), sg_e));
                     acc_add<NL>(acc_e, se, ee.e[0] * 3 + d, q0);
                     acc_add<NL>(acc_e, se, ee.e[1] * 3 + d, q0);
                     acc_add<NL>(acc_e, se, ee.e[2] * 3 + d, q0);
-                    const Lq q1 = FX::q(F::sgn(N1[d], -s), sg_e);
                     acc_add<NL>(acc_e, se, ee.e[3] * 3 + d, q1);
                     acc_add<NL>(acc_e, se, ee.e[4] * 3 + d, q1);
-                    acc_add<NL>(acc_e, se, ee.e[5] * 3 + d, FX::q(F::sgn(N2[d], -s), sg_e));
+                    acc_add<NL>(acc_e, se, ee.e[5] * 3 + d, q2);
                 }
                 const Lq qv = FX::q(F::sgn(det, s), sg_v);
 #pragma unroll
                 for (int r = 0; r < 4; r++) acc_add<NL>(acc_v, sv, cn.v[r], qv);
             }
             if (WHAT & DO_ADJ) {
-                V W0[3], W1[3], W2[3];
+                // 12 g_k = -s (A''_{k+1} x X_{k+2} - A''_{k+2} x X_{k+1}), k = 1, 2, 3
+                // (indices cyclic, X = (a, b, c)), with A''_k = A_k - (C/4) X_k:
+                // the (C/4) X_k terms carry the volume part s C/24 N_k of g_k.
+                // The factor 1/12 is applied when the sums are written; node
+                // 0 takes -(g_1 + g_2 + g_3), summed as integers.
+                V W0[3], Ar[3][3], Xr[3][3];
+                const V Cq = F::quarter(F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]])));
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     W0[d] = F::add(F::add(ws[ee.e[0] * 3 + d], ws[ee.e[1] * 3 + d]), ws[ee.e[2] * 3 + d]);
-                    W1[d] = F::add(ws[ee.e[3] * 3 + d], ws[ee.e[4] * 3 + d]);
-                    W2[d] = ws[ee.e[5] * 3 + d];
-                }
-                V A1[3], A2[3], A3[3];
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    A1[d] = F::sub(W1[d], W0[d]);
-                    A2[d] = F::sub(W2[d], W0[d]);
-                    A3[d] = F::sgn(W0[d], -1.f);
-                }
-                V Cs = F::add(F::add(cs[cn.v[0]], cs[cn.v[1]]), F::add(cs[cn.v[2]], cs[cn.v[3]]));
-                const V f12 = F::cst(-1.0 / 12.0), f24 = F::cst(1.0 / 24.0);
-                V h = F::sgn(F::mul(Cs, f24), s);
-                // g_k for k = 1, 2, 3: one loop body with the operand vectors
-                // rotated by one position per iteration
-                V Ar[3][3], Xr[3][3], Nr[3][3];
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    Ar[0][d] = A1[d]; Ar[1][d] = A2[d]; Ar[2][d] = A3[d];
                     Xr[0][d] = a[d]; Xr[1][d] = b[d]; Xr[2][d] = c[d];
-                    Nr[0][d] = N1[d]; Nr[1][d] = N2[d]; Nr[2][d] = N3[d];
+                    Ar[0][d] = F::sub(F::add(ws[ee.e[3] * 3 + d], ws[ee.e[4] * 3 + d]), F::add(W0[d], F::mul(Cq, a[d])));
+                    Ar[1][d] = F::sub(ws[ee.e[5] * 3 + d], F::add(W0[d], F::mul(Cq, b[d])));
+                    Ar[2][d] = F::sgn(F::add(W0[d], F::mul(Cq, c[d])), -1.f);
                 }
                 int vr0 = cn.v[1], vr1 = cn.v[2], vr2 = cn.v[3];
-                V gs[3] = {F::cst(0.0), F::cst(0.0), F::cst(0.0)};
+                Lq g0[3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll 1
                 for (int k = 0; k < 3; k++) {
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
                         const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                        V g = F::sub(F::det2(Ar[1][d1], Xr[2][d2], Ar[1][d2], Xr[2][d1]),
-                                     F::det2(Ar[2][d1], Xr[1][d2], Ar[2][d2], Xr[1][d1]));
-                        const V gk = F::add(F::sgn(F::mul(g, f12), s), F::mul(h, Nr[0][d]));
-                        acc_add<NL>(acc_g, sgs, vr0 * 3 + d, FX::q(gk, sg_g));
-                        gs[d] = F::add(gs[d], gk);
+                        const V g = F::sub(F::det2(Ar[1][d1], Xr[2][d2], Ar[1][d2], Xr[2][d1]),
+                                           F::det2(Ar[2][d1], Xr[1][d2], Ar[2][d2], Xr[1][d1]));
+                        const Lq q = FX::q(F::sgn(g, -s), sg_g);
+                        acc_add<NL>(acc_g, sgs, vr0 * 3 + d, q);
+                        lq_sub(g0[d], q);
                     }
                     // rotate: position 0 takes the next k
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
                         V t0 = Ar[0][d]; Ar[0][d] = Ar[1][d]; Ar[1][d] = Ar[2][d]; Ar[2][d] = t0;
                         V t1 = Xr[0][d]; Xr[0][d] = Xr[1][d]; Xr[1][d] = Xr[2][d]; Xr[2][d] = t1;
-                        V t2 = Nr[0][d]; Nr[0][d] = Nr[1][d]; Nr[1][d] = Nr[2][d]; Nr[2][d] = t2;
                     }
                     const int tv = vr0; vr0 = vr1; vr1 = vr2; vr2 = tv;
                 }
 #pragma unroll
-                for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d, FX::q(F::sgn(gs[d], -1.f), sg_g));
+                for (int d = 0; d < 3; d++) acc_add<NL>(acc_g, sgs, cn.v[0] * 3 + d, g0[d]);
             }
         } else {
             V a[2], b[2];
@@ -499,10 +494,11 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
                 V n2[2] = {F::sgn(a[1], s), F::sgn(a[0], -s)};
 #pragma unroll
                 for (int d = 0; d < 2; d++) {
-                    const Lq q0 = FX::q(F::sgn(F::add(n1[d], n2[d]), -1.f), sg_e);
+                    const Lq q1 = FX::q(n1[d], sg_e);
+                    const Lq q0 = lq_neg_sum(q1, FX::q(n2[d], sg_e), Lq{0, 0, 0});
                     acc_add<NL>(acc_e, se, ee.e[0] * 2 + d, q0);
                     acc_add<NL>(acc_e, se, ee.e[1] * 2 + d, q0);
-                    acc_add<NL>(acc_e, se, ee.e[2] * 2 + d, FX::q(n1[d], sg_e));
+                    acc_add<NL>(acc_e, se, ee.e[2] * 2 + d, q1);
                 }
                 const Lq qv = FX::q(F::sgn(det, s), sg_v);
 #pragma unroll
@@ -524,12 +520,13 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
                 const V gay = F::add(F::sgn(F::mul(A2[0], f3), s), F::sgn(F::mul(h, b[0]), -1.f));
                 const V gbx = F::add(F::sgn(F::mul(A1[1], f3), s), F::sgn(F::mul(h, a[1]), -1.f));
                 const V gby = F::add(F::sgn(F::mul(A1[0], f3), -s), F::mul(h, a[0]));
-                acc_add<NL>(acc_g, sgs, cn.v[1] * 2, FX::q(gax, sg_g));
-                acc_add<NL>(acc_g, sgs, cn.v[1] * 2 + 1, FX::q(gay, sg_g));
-                acc_add<NL>(acc_g, sgs, cn.v[2] * 2, FX::q(gbx, sg_g));
-                acc_add<NL>(acc_g, sgs, cn.v[2] * 2 + 1, FX::q(gby, sg_g));
-                acc_add<NL>(acc_g, sgs, cn.v[0] * 2, FX::q(F::sgn(F::add(gax, gbx), -1.f), sg_g));
-                acc_add<NL>(acc_g, sgs, cn.v[0] * 2 + 1, FX::q(F::sgn(F::add(gay, gby), -1.f), sg_g));
+                const Lq qax = FX::q(gax, sg_g), qay = FX::q(gay, sg_g), qbx = FX::q(gbx, sg_g), qby = FX::q(gby, sg_g);
+                acc_add<NL>(acc_g, sgs, cn.v[1] * 2, qax);
+                acc_add<NL>(acc_g, sgs, cn.v[1] * 2 + 1, qay);
+                acc_add<NL>(acc_g, sgs, cn.v[2] * 2, qbx);
+                acc_add<NL>(acc_g, sgs, cn.v[2] * 2 + 1, qby);
+                acc_add<NL>(acc_g, sgs, cn.v[0] * 2, lq_neg_sum(qax, qbx, Lq{0, 0, 0}));
+                acc_add<NL>(acc_g, sgs, cn.v[0] * 2 + 1, lq_neg_sum(qay, qby, Lq{0, 0, 0}));
             }
         }
     }
@@ -563,9 +560,11 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
 #pragma unroll
                 for (int d = 0; d < 3; d++)
                     WB[d] = F::add(F::add(ws[f.e[0] * 3 + d], ws[f.e[1] * 3 + d]), ws[f.e[2] * 3 + d]);
-                const V f24 = F::cst(1.0 / 24.0);
-                // boundary-normal weights: K = 1/3 sum of bw at the face's nodes
-                V K[3];
+                // 12 x the gradient, like the element terms: 1/2 (t x W_B) and
+                // 1/2 (W_B x u) from the edges' n_B/12, and with boundary-normal
+                // weights K = 1/3 sum of bw at the face's nodes, 12 (1/2) (t x K)
+                // = t x K6, K6 = 6 K = 2 sum bw
+                V K6[3];
                 const bool hasK = A.bwa.bw != nullptr;
                 if (hasK) {
                     double Kd[3] = {0.0, 0.0, 0.0};
@@ -576,17 +575,17 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
                         for (int d = 0; d < 3; d++) Kd[d] += A.bwa.bw[3 * bi + d];
                     }
 #pragma unroll
-                    for (int d = 0; d < 3; d++) K[d] = F::from_double(Kd[d] / 3.0);
+                    for (int d = 0; d < 3; d++) K6[d] = F::from_double(2.0 * Kd[d]);
                     if (!(isfinite(Kd[0]) && isfinite(Kd[1]) && isfinite(Kd[2]))) atomicOr(red + 11, 1u);
                 }
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
                     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-                    V gq = F::mul(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]), f24);
-                    V gr = F::mul(F::det2(WB[d1], u[d2], WB[d2], u[d1]), f24);
+                    V gq = F::half(F::det2(tt[d1], WB[d2], tt[d2], WB[d1]));
+                    V gr = F::half(F::det2(WB[d1], u[d2], WB[d2], u[d1]));
                     if (hasK) {
-                        gq = F::add(gq, F::half(F::det2(tt[d1], K[d2], tt[d2], K[d1])));
-                        gr = F::add(gr, F::half(F::det2(K[d1], u[d2], K[d2], u[d1])));
+                        gq = F::add(gq, F::det2(tt[d1], K6[d2], tt[d2], K6[d1]));
+                        gr = F::add(gr, F::det2(K6[d1], u[d2], K6[d2], u[d1]));
                     }
                     acc_add<NL>(acc_g, sgs, f.v[1] * 3 + d, FX::q(gq, sg_g));
                     acc_add<NL>(acc_g, sgs, f.v[2] * 3 + d, FX::q(gr, sg_g));
@@ -748,7 +747,7 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     if (WHAT & DO_ADJ) {
         for (int q = tid; q < nnodes * DIM; q += NTH) {
             const int i = q / DIM, d = q - i * DIM;
-            const double v = outv(acc_g, sgs, q, sg_g, 1.0);
+            const double v = outv(acc_g, sgs, q, sg_g, DIM == 3 ? 1.0 / 12.0 : 1.0);
             if (i < ti.n_own) A.grad[int64_t(ti.node0) * DIM + q] = v;
             else A.rec_n[(int64_t(ti.halo_off) + i - ti.n_own) * REC_DOUBLES + 1 + d] = v;
         }
@@ -854,9 +853,13 @@ __global__ void __launch_bounds__(NTH, NTH == NT ? scatter_min_ctas<PREC, WHAT>(
 }
 
 inline int check_valence(int val_e, int val_v) {
-    // a limb plane entry holds < 1024 contributions of magnitude <= 2^21
-    if (val_e > 1000 || val_v > 250)
-        return fail(EM_ERR_ARG, "tiled path: an edge with more than 1000 elements or a node with more than 250 "
+    // A limb plane entry holds the sum of fewer than 1024 limbs of magnitude
+    // <= 2^21.  Per element an edge entry receives up to 3 of them (the
+    // integer sum -(q1 + q2 + q3) at the edges of node 0) and a boundary face
+    // one; a node's gradient entry receives up to 3 per element (node 0) and
+    // one per boundary face, of which a node has at most 3 per element.
+    if (val_e > 340 || val_v > 170)
+        return fail(EM_ERR_ARG, "tiled path: an edge with more than 340 elements or a node with more than 170 "
                                 "elements exceeds its fixed-point headroom; use the gather path");
     return EM_OK;
 }

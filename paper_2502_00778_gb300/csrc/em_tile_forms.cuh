@@ -31,6 +31,7 @@ struct Form<EM_PREC_FP64> {
     static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return __fma_rn(p, q, -__dmul_rn(r, s)); }
     static __device__ __forceinline__ V sgn(V a, float s) { return s < 0.f ? -a : a; }
     static __device__ __forceinline__ V half(V a) { return __dmul_rn(0.5, a); }
+    static __device__ __forceinline__ V quarter(V a) { return __dmul_rn(0.25, a); }
     static __device__ __forceinline__ float sign_of(V a) { return a > 0.0 ? 1.f : -1.f; }
     static __device__ __forceinline__ V from_double(double d) { return d; }
     static __device__ __forceinline__ V cst(double d) { return d; }
@@ -52,6 +53,7 @@ struct Form<EM_PREC_DW> {
     static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return dw_det2(p, q, r, s); }
     static __device__ __forceinline__ V sgn(V a, float s) { return dw_sgn(a, s); }
     static __device__ __forceinline__ V half(V a) { return {__fmul_rn(0.5f, a.h), __fmul_rn(0.5f, a.l)}; }
+    static __device__ __forceinline__ V quarter(V a) { return {__fmul_rn(0.25f, a.h), __fmul_rn(0.25f, a.l)}; }
     static __device__ __forceinline__ float sign_of(V a) { return (a.h > 0.f || (a.h == 0.f && a.l > 0.f)) ? 1.f : -1.f; }
     static __device__ __forceinline__ V from_double(double d) { return dw_from_double(d); }
     static __device__ __forceinline__ V cst(double d) { return dw_from_double(d); }
@@ -76,6 +78,7 @@ struct Form<EM_PREC_MIXED> {
     static __device__ __forceinline__ V det2(V p, V q, V r, V s) { return fmaf(p, q, -r * s); }
     static __device__ __forceinline__ V sgn(V a, float s) { return a * s; }
     static __device__ __forceinline__ V half(V a) { return 0.5f * a; }
+    static __device__ __forceinline__ V quarter(V a) { return 0.25f * a; }
     static __device__ __forceinline__ float sign_of(V a) { return a > 0.f ? 1.f : -1.f; }
     static __device__ __forceinline__ V from_double(double d) { return f_from_double(d); }
     static __device__ __forceinline__ V cst(double d) { return f_from_double(d); }
@@ -145,6 +148,17 @@ __device__ __forceinline__ int fx_round(float t, float& rem) {
     const float y = __fadd_rn(t, FX_MAGIC);
     rem = __fsub_rn(t, __fsub_rn(y, FX_MAGIC));
     return __float_as_int(y) - 0x4B400000;
+}
+
+// -(a + b + c) and x -= q, limb by limb: exact integer sums of quantised
+// values (each limb stays within 3 x 2^21)
+__device__ __forceinline__ Lq lq_neg_sum(const Lq& a, const Lq& b, const Lq& c) {
+    return {-(a.a + b.a + c.a), -(a.b + b.b + c.b), -(a.c + b.c + c.c)};
+}
+__device__ __forceinline__ void lq_sub(Lq& x, const Lq& q) {
+    x.a -= q.a;
+    x.b -= q.b;
+    x.c -= q.c;
 }
 
 template <int NL>
