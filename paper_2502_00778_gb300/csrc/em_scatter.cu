@@ -223,33 +223,58 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     }
 
     // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
+    // Each thread takes up to SB nodes and SBW edges per round.  It first
+    // requests the halo indices of all of them (owned rows need none), then all
+    // their gathers, and converts last, so a round costs two dependent trips to
+    // L2 / HBM however many lists it covers.  The tile origin is loaded with
+    // the indices and only replaced when it is not finite (rare).
+    constexpr int SB = NTH > NT ? 1 : 2, SBW = (WHAT & DO_ADJ) ? 6 : 1;
     double org[DIM];
-    tile_origin<DIM>(A.x, ti.node0, ti.n_own, org);
-    // gathers are issued in batches of SB per thread so that several loads are
-    // in flight before the first one is used
-    constexpr int SB = 4, SBW = 8;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
     unsigned wm = 0u, cm = 0u;
     float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
     bool nf = false;     // a staged value is non-finite (staged as NaN)
-    for (int i0 = tid; i0 < nnodes; i0 += SB * NTH) {
-        int64_t v[SB];
+    const int n_rounds = max((nnodes + SB * NTH - 1) / (SB * NTH),
+                             (WHAT & DO_ADJ) ? (nedges + SBW * NTH - 1) / (SBW * NTH) : 0);
+    for (int r = 0; r < n_rounds; r++) {
+        int vn[SB], ve[SBW];
 #pragma unroll
         for (int u = 0; u < SB; u++) {
-            const int i = i0 + u * NTH;
-            v[u] = i >= nnodes ? -1 : (i < ti.n_own ? int64_t(ti.node0) + i : int64_t(halo[i - ti.n_own]));
+            const int i = r * SB * NTH + tid + u * NTH;
+            vn[u] = i >= nnodes ? -1 : (i < ti.n_own ? ti.node0 + i : halo[i - ti.n_own]);
         }
-        double xv[SB][DIM], cv[SB];
+        if (WHAT & DO_ADJ) {
+#pragma unroll
+            for (int u = 0; u < SBW; u++) {
+                const int i = r * SBW * NTH + tid + u * NTH;
+                ve[u] = i >= nedges ? -1 : (i < ti.n_eo ? ti.edge0 + i : hedge[i - ti.n_eo]);
+            }
+        }
+        double xv[SB][DIM], cv[SB], wv[SBW][DIM];
 #pragma unroll
         for (int u = 0; u < SB; u++) {
-            if (v[u] < 0) continue;
+            if (vn[u] < 0) continue;
 #pragma unroll
-            for (int d = 0; d < DIM; d++) xv[u][d] = A.x[v[u] * DIM + d];
-            if (WHAT & DO_ADJ) cv[u] = A.c ? A.c[v[u]] : 0.0;
+            for (int d = 0; d < DIM; d++) xv[u][d] = A.x[int64_t(vn[u]) * DIM + d];
+            if (WHAT & DO_ADJ) cv[u] = A.c ? A.c[vn[u]] : 0.0;
+        }
+        if (WHAT & DO_ADJ) {
+#pragma unroll
+            for (int u = 0; u < SBW; u++)
+                if (ve[u] >= 0)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) wv[u][d] = A.w[int64_t(ve[u]) * DIM + d];
+        }
+        if (r == 0) {
+#pragma unroll
+            for (int d = 0; d < DIM; d++)
+                if (!isfinite(org[d])) org[d] = tile_origin_component<DIM>(A.x, ti.node0, ti.n_own, d);
         }
 #pragma unroll
         for (int u = 0; u < SB; u++) {
-            if (v[u] < 0) continue;
-            const int i = i0 + u * NTH;
+            if (vn[u] < 0) continue;
+            const int i = r * SB * NTH + tid + u * NTH;
 #pragma unroll
             for (int d = 0; d < DIM; d++) {
                 const C xc = finite_or_nan(F::coord(xv[u][d], org[d]));
@@ -264,25 +289,11 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
                 cm = max(cm, FX::mag(c1));
             }
         }
-    }
-    if (WHAT & DO_ADJ) {
-        for (int i0 = tid; i0 < nedges; i0 += SBW * NTH) {
-            int64_t e[SBW];
+        if (WHAT & DO_ADJ) {
 #pragma unroll
             for (int u = 0; u < SBW; u++) {
-                const int i = i0 + u * NTH;
-                e[u] = i >= nedges ? -1 : (i < ti.n_eo ? int64_t(ti.edge0) + i : int64_t(hedge[i - ti.n_eo]));
-            }
-            double wv[SBW][DIM];
-#pragma unroll
-            for (int u = 0; u < SBW; u++)
-                if (e[u] >= 0)
-#pragma unroll
-                    for (int d = 0; d < DIM; d++) wv[u][d] = A.w[e[u] * DIM + d];
-#pragma unroll
-            for (int u = 0; u < SBW; u++) {
-                if (e[u] < 0) continue;
-                const int i = i0 + u * NTH;
+                if (ve[u] < 0) continue;
+                const int i = r * SBW * NTH + tid + u * NTH;
 #pragma unroll
                 for (int d = 0; d < DIM; d++) {
                     const V w1 = finite_or_nan(F::from_double(wv[u][d]));

@@ -107,13 +107,15 @@ __device__ __forceinline__ dw finite_or_nan(dw v) { return v; }
 // coordinate is finite (0 if none is), so that one non-finite coordinate does
 // not reach the other staged nodes through the subtraction.
 template <int DIM>
+__device__ __forceinline__ double tile_origin_component(const double* x, int node0, int n_own, int d) {
+    double o = x[int64_t(node0) * DIM + d];
+    for (int k = 1; !isfinite(o) && k < n_own; k++) o = x[(int64_t(node0) + k) * DIM + d];
+    return isfinite(o) ? o : 0.0;
+}
+template <int DIM>
 __device__ __forceinline__ void tile_origin(const double* x, int node0, int n_own, double* org) {
 #pragma unroll
-    for (int d = 0; d < DIM; d++) {
-        double o = x[int64_t(node0) * DIM + d];
-        for (int k = 1; !isfinite(o) && k < n_own; k++) o = x[(int64_t(node0) + k) * DIM + d];
-        org[d] = isfinite(o) ? o : 0.0;
-    }
+    for (int d = 0; d < DIM; d++) org[d] = tile_origin_component<DIM>(x, node0, n_own, d);
 }
 
 
@@ -184,6 +186,26 @@ __device__ __forceinline__ double pow2d(int k) {
 
 __device__ __forceinline__ int sg_clamp(int sg, int lo, int hi) { return sg > hi ? hi : (sg < lo ? lo : sg); }
 
+// q * 2^-sg as a double, rounded to nearest even, with integer instructions
+// only (the int64 -> double conversion instruction runs on the FP64 pipe,
+// which the output pass of a tile would otherwise saturate).  |q| < 2^62 and
+// sg within the forms' [LO, HI] ranges keep the result a normal double.
+// |q| is shifted so that its leading one is bit 63; its upper 53 bits are
+// the mantissa, rounded on the 11 bits below; a carry out of the rounding
+// (mantissa 2^53) moves into the exponent field through the addition.
+__device__ __forceinline__ double fx_to_double(long long q, int sg) {
+    if (q == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ull;
+    unsigned long long a = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    const int lz = __clzll((long long)a);
+    a <<= lz;
+    unsigned long long m = a >> 11;
+    const unsigned rem = (unsigned)(a & 0x7ffull);
+    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+    const long long field = 1023 + 63 - lz - sg;   // biased exponent of 2^(63 - lz - sg)
+    return __longlong_as_double((long long)((((unsigned long long)(field - 1)) << 52) + m + sign));
+}
+
 // Magnitudes as order-preserving 32-bit keys: the upper word of |v| as an
 // IEEE double (exponent and 20 mantissa bits).  Non-negative doubles order
 // like their bit patterns, so an integer max gives the max magnitude.  Every
@@ -212,7 +234,7 @@ struct Fix<EM_PREC_FP64> {
     }
     static __device__ __forceinline__ unsigned mag(double v) { return mkey(v); }
     static __device__ __forceinline__ double out(long long q, int sg, double sc) {
-        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+        return sc == 1.0 ? fx_to_double(q, sg) : __dmul_rn(fx_to_double(q, sg), sc);
     }
 };
 
@@ -234,9 +256,10 @@ struct Fix<EM_PREC_DW> {
     static __device__ __forceinline__ unsigned mag(dw v) {
         return mkey(f_to_double((fabsf(v.h) + fabsf(v.l)) * 1.000001f));
     }
-    // once per output: the FP64 pipe is otherwise idle in this form
+    // once per output: the conversion runs on the integer pipe, one DMUL
+    // applies the output factor
     static __device__ __forceinline__ double out(long long q, int sg, double sc) {
-        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+        return sc == 1.0 ? fx_to_double(q, sg) : __dmul_rn(fx_to_double(q, sg), sc);
     }
 };
 
@@ -251,7 +274,7 @@ struct Fix<EM_PREC_MIXED> {
     }
     static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
     static __device__ __forceinline__ double out(long long q, int sg, double sc) {
-        return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), sc));
+        return sc == 1.0 ? fx_to_double(q, sg) : __dmul_rn(fx_to_double(q, sg), sc);
     }
 };
 
