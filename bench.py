@@ -676,9 +676,12 @@ def run_ours(args):
 
     # ---- FP64 ALU ceiling of the native-FP64 forms ----
     fp64_alu = {}
-    for key, kern in (("fwd:atomic/fp64", "k_fwd_atomic3<fp64>"), ("fwd:tiled/fp64", "k_stile<3,fp64,fwd>"),
-                      ("tiled/fp64", "k_stile<3,fp64,fwd+adj>")):
-        ops = fp64_ops(kern)
+    for key, kerns in (("fwd:atomic/fp64", ("k_fwd_atomic3<fp64>",)),
+                       ("atomic/fp64", ("k_fwd_atomic3<fp64>", "k_adj_atomic3<fp64>")),
+                       ("fwd:tiled/fp64", ("k_stile<3,fp64,fwd>",)), ("tiled/fp64", ("k_stile<3,fp64,fwd+adj>",))):
+        counts = [fp64_ops(k) for k in kerns]
+        ops = sum(counts) if all(counts) else None
+        kern = "+".join(kerns)
         f = forms.get(key, {})
         if ops and "ms_per_step" in f:
             ach = ops * m.n_elems / (f["ms_per_step"] * 1e-3)
