@@ -163,163 +163,10 @@ __device__ void prefetch_stile_l2(const SArgs& A, int t2, int lane) {
     }
 }
 
-// ---- a scatter tile in phases ------------------------------------------------
-// stage_issue  requests the tile's staging data (halo indices first, then the
-//              gathers of the first round) into registers;
-// stage_commit converts and stores them in shared memory (later rounds, rare,
-//              load and store in one go) and records the staged magnitudes;
-// tile_body    clears the accumulators, bounds the element extent, derives
-//              the scales and runs the element and boundary loops;
-// tile_output  writes owned targets as outputs, halo targets as records.
-// The one-tile path runs them in this order.  The persistent path issues the
-// next tile's staging loads before the current tile's output pass, so that
-// their latency is hidden behind it (the staging buffers are free once the
-// element and boundary loops are done; the accumulators are not).
-template <int DIM, int PREC, int WHAT, int NTH>
-struct SStage {
-    static constexpr int SB = 2, SBW = (WHAT & DO_ADJ) ? 6 : 1, EB = 8;
-    static constexpr bool HOIST = NTH > NT;
-    int vn[SB], ve[SBW];
-    double xv[SB][DIM], cv[SB], wv[SBW][DIM], org[DIM];
-    ElemConn ecb[HOIST ? EB : 1];   // first extent-pass records (512-thread tiles)
-};
-
-struct SScales {
-    int sg_e, sg_v, sg_b, sg_g;
-    bool range_bad, poison;
-};
-
-// round r of the staging gathers of tile t into R (indices, then data)
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void stage_load(const SArgs& A, const STile& ti, const int32_t* halo,
-                                           const int32_t* hedge, int r, SStage<DIM, PREC, WHAT, NTH>& R) {
-    using S = SStage<DIM, PREC, WHAT, NTH>;
-    const int tid = threadIdx.x;
-    const int nnodes = ti.n_own + ti.n_halo, nedges = ti.n_eo + ti.n_hedge;
-#pragma unroll
-    for (int u = 0; u < S::SB; u++) {
-        const int i = r * S::SB * NTH + tid + u * NTH;
-        R.vn[u] = i >= nnodes ? -1 : (i < ti.n_own ? ti.node0 + i : halo[i - ti.n_own]);
-    }
-    if (WHAT & DO_ADJ) {
-#pragma unroll
-        for (int u = 0; u < S::SBW; u++) {
-            const int i = r * S::SBW * NTH + tid + u * NTH;
-            R.ve[u] = i >= nedges ? -1 : (i < ti.n_eo ? ti.edge0 + i : hedge[i - ti.n_eo]);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < S::SB; u++) {
-        if (R.vn[u] < 0) continue;
-#pragma unroll
-        for (int d = 0; d < DIM; d++) R.xv[u][d] = A.x[int64_t(R.vn[u]) * DIM + d];
-        if (WHAT & DO_ADJ) R.cv[u] = A.c ? A.c[R.vn[u]] : 0.0;
-    }
-    if (WHAT & DO_ADJ) {
-#pragma unroll
-        for (int u = 0; u < S::SBW; u++)
-            if (R.ve[u] >= 0)
-#pragma unroll
-                for (int d = 0; d < DIM; d++) R.wv[u][d] = A.w[int64_t(R.ve[u]) * DIM + d];
-    }
-}
-
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void stage_issue(const SArgs& A, int t, SStage<DIM, PREC, WHAT, NTH>& R) {
-    using S = SStage<DIM, PREC, WHAT, NTH>;
-    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
-    const STile ti = plan_at<STile>(A.plan, H->off_stiles)[t];
-    const int tid = threadIdx.x;
-    if constexpr (S::HOIST) {
-        const ElemConn* conn = plan_at<ElemConn>(A.plan, H->off_sconn) + ti.elem_off;
-#pragma unroll
-        for (int u = 0; u < S::EB; u++)
-            if (tid + u * NTH < ti.n_el) R.ecb[u] = conn[tid + u * NTH];
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; d++) R.org[d] = A.x[int64_t(ti.node0) * DIM + d];
-    stage_load<DIM, PREC, WHAT, NTH>(A, ti, plan_at<int32_t>(A.plan, H->off_shalo) + ti.halo_off,
-                                     plan_at<int32_t>(A.plan, H->off_shedge) + ti.hedge_off, 0, R);
-}
-
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void stage_commit(const SArgs& A, int t, SStage<DIM, PREC, WHAT, NTH>& R, char* smem) {
-    using S = SStage<DIM, PREC, WHAT, NTH>;
-    using F = Form<PREC>;
-    using FX = Fix<PREC>;
-    using C = typename F::C;
-    using V = typename F::V;
-    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
-    const STile ti = plan_at<STile>(A.plan, H->off_stiles)[t];
-    const int32_t* halo = plan_at<int32_t>(A.plan, H->off_shalo) + ti.halo_off;
-    const int32_t* hedge = plan_at<int32_t>(A.plan, H->off_shedge) + ti.hedge_off;
-    const SmemS L = s_layout<DIM, PREC, WHAT>(A.D);
-    C* xs = reinterpret_cast<C*>(smem + L.xs);
-    V* ws = reinterpret_cast<V*>(smem + L.ws);
-    V* cs = reinterpret_cast<V*>(smem + L.cs);
-    unsigned* wred = reinterpret_cast<unsigned*>(smem + L.red) + 16;
-    const int tid = threadIdx.x;
-    const int nnodes = ti.n_own + ti.n_halo, nedges = ti.n_eo + ti.n_hedge;
-    // the tile origin: its first owned node, replaced when not finite (rare)
-#pragma unroll
-    for (int d = 0; d < DIM; d++)
-        if (!isfinite(R.org[d])) R.org[d] = tile_origin_component<DIM>(A.x, ti.node0, ti.n_own, d);
-    unsigned wm = 0u, cm = 0u;
-    float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
-    bool nf = false;     // a staged value is non-finite (staged as NaN)
-    const int n_rounds = max((nnodes + S::SB * NTH - 1) / (S::SB * NTH),
-                             (WHAT & DO_ADJ) ? (nedges + S::SBW * NTH - 1) / (S::SBW * NTH) : 0);
-    for (int r = 0; r < n_rounds; r++) {
-        if (r > 0) stage_load<DIM, PREC, WHAT, NTH>(A, ti, halo, hedge, r, R);
-#pragma unroll
-        for (int u = 0; u < S::SB; u++) {
-            if (R.vn[u] < 0) continue;
-            const int i = r * S::SB * NTH + tid + u * NTH;
-#pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const C xc = finite_or_nan(F::coord(R.xv[u][d], R.org[d]));
-                xs[i * DIM + d] = xc;
-                nf |= is_nan(xc);
-                if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
-            }
-            if (WHAT & DO_ADJ) {
-                const V c1 = finite_or_nan(F::from_double(R.cv[u]));
-                cs[i] = c1;
-                nf |= is_nan(c1);
-                cm = max(cm, FX::mag(c1));
-            }
-        }
-        if (WHAT & DO_ADJ) {
-#pragma unroll
-            for (int u = 0; u < S::SBW; u++) {
-                if (R.ve[u] < 0) continue;
-                const int i = r * S::SBW * NTH + tid + u * NTH;
-#pragma unroll
-                for (int d = 0; d < DIM; d++) {
-                    const V w1 = finite_or_nan(F::from_double(R.wv[u][d]));
-                    ws[i * DIM + d] = w1;
-                    nf |= is_nan(w1);
-                    wm = max(wm, FX::mag(w1));
-                }
-            }
-        }
-    }
-    if (WHAT & DO_ADJ) {
-        block_max(wred, 1, wm);
-        block_max(wred, 2, cm);
-    }
-    if constexpr (PREC != EM_PREC_FP64) block_max(wred, 3, mkey(f_to_double(xl)));
-    block_max(wred, 4, nf ? 1u : 0u);
-}
-
-// Runs after a barrier that follows stage_commit (and, on the persistent
-// path, the previous tile's output pass).  Returns this thread's copy of the
-// tile's scales; every accumulator is complete when it returns.
-// pf(lane) is called by the last warp once the extent is known: it may
-// prefetch a later tile's inputs into L2 while the other warps compute.
-template <int DIM, int PREC, int WHAT, int NTH, bool HOIST, class PF>
-__device__ __forceinline__ SScales tile_body(const SArgs& A, int t, const ElemConn* ecb, char* smem, const PF& pf) {
-    constexpr int EB = SStage<DIM, PREC, WHAT, NTH>::EB;
+// pf(lane) is called by the last warp once the tile's staging is done: it may
+// prefetch a later tile's inputs into L2 while the other warps compute
+template <int DIM, int PREC, int WHAT, int NTH, class PF>
+__device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, const PF& pf) {
     using F = Form<PREC>;
     using FX = Fix<PREC>;
     using C = typename F::C;
@@ -352,17 +199,118 @@ __device__ __forceinline__ SScales tile_body(const SArgs& A, int t, const ElemCo
     const int nnodes = ti.n_own + ti.n_halo;
     const int nedges = ti.n_eo + ti.n_hedge;
     const int nbn = ti.n_bo + ti.n_hbo;
-    (void)halo;
-    (void)hedge;
 
     // ---- clear the accumulator block (16-byte stores) -------------------------
-    // (the planes are first used after the extent barrier below)
     if (tid < 16) red[tid] = 0u;
     {
         int4* a4 = reinterpret_cast<int4*>(smem + L.acc_e);
         const int n4 = (int)((L.red - L.acc_e) / 16);
         for (int q = tid; q < n4; q += NTH) a4[q] = make_int4(0, 0, 0, 0);
     }
+    // (no barrier: the planes are first used after the staging and extent
+    // barriers below)
+
+    // 512-thread tiles (one CTA per SM, nothing hides their latency): this
+    // thread's first element records of the extent pass below are requested
+    // now, so that they arrive while the staging gathers are in flight
+    constexpr int EB = 8;
+    constexpr bool HOIST = NTH > NT;
+    ElemConn ecb[HOIST ? EB : 1];
+    if constexpr (HOIST) {
+#pragma unroll
+        for (int u = 0; u < EB; u++)
+            if (tid + u * NTH < ti.n_el) ecb[u] = conn[tid + u * NTH];
+    }
+
+    // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
+    // Each thread takes up to SB nodes and SBW edges per round.  It first
+    // requests the halo indices of all of them (owned rows need none), then all
+    // their gathers, and converts last, so a round costs two dependent trips to
+    // L2 / HBM however many lists it covers.  The tile origin is loaded with
+    // the indices and only replaced when it is not finite (rare).
+    constexpr int SB = NTH > NT ? 1 : 2, SBW = (WHAT & DO_ADJ) ? 6 : 1;
+    double org[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
+    unsigned wm = 0u, cm = 0u;
+    float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
+    bool nf = false;     // a staged value is non-finite (staged as NaN)
+    const int n_rounds = max((nnodes + SB * NTH - 1) / (SB * NTH),
+                             (WHAT & DO_ADJ) ? (nedges + SBW * NTH - 1) / (SBW * NTH) : 0);
+    for (int r = 0; r < n_rounds; r++) {
+        int vn[SB], ve[SBW];
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            const int i = r * SB * NTH + tid + u * NTH;
+            vn[u] = i >= nnodes ? -1 : (i < ti.n_own ? ti.node0 + i : halo[i - ti.n_own]);
+        }
+        if (WHAT & DO_ADJ) {
+#pragma unroll
+            for (int u = 0; u < SBW; u++) {
+                const int i = r * SBW * NTH + tid + u * NTH;
+                ve[u] = i >= nedges ? -1 : (i < ti.n_eo ? ti.edge0 + i : hedge[i - ti.n_eo]);
+            }
+        }
+        double xv[SB][DIM], cv[SB], wv[SBW][DIM];
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            if (vn[u] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) xv[u][d] = A.x[int64_t(vn[u]) * DIM + d];
+            if (WHAT & DO_ADJ) cv[u] = A.c ? A.c[vn[u]] : 0.0;
+        }
+        if (WHAT & DO_ADJ) {
+#pragma unroll
+            for (int u = 0; u < SBW; u++)
+                if (ve[u] >= 0)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) wv[u][d] = A.w[int64_t(ve[u]) * DIM + d];
+        }
+        if (r == 0) {
+#pragma unroll
+            for (int d = 0; d < DIM; d++)
+                if (!isfinite(org[d])) org[d] = tile_origin_component<DIM>(A.x, ti.node0, ti.n_own, d);
+        }
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            if (vn[u] < 0) continue;
+            const int i = r * SB * NTH + tid + u * NTH;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const C xc = finite_or_nan(F::coord(xv[u][d], org[d]));
+                xs[i * DIM + d] = xc;
+                nf |= is_nan(xc);
+                if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
+            }
+            if (WHAT & DO_ADJ) {
+                const V c1 = finite_or_nan(F::from_double(cv[u]));
+                cs[i] = c1;
+                nf |= is_nan(c1);
+                cm = max(cm, FX::mag(c1));
+            }
+        }
+        if (WHAT & DO_ADJ) {
+#pragma unroll
+            for (int u = 0; u < SBW; u++) {
+                if (ve[u] < 0) continue;
+                const int i = r * SBW * NTH + tid + u * NTH;
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const V w1 = finite_or_nan(F::from_double(wv[u][d]));
+                    ws[i * DIM + d] = w1;
+                    nf |= is_nan(w1);
+                    wm = max(wm, FX::mag(w1));
+                }
+            }
+        }
+    }
+    if (WHAT & DO_ADJ) {
+        block_max(wred, 1, wm);
+        block_max(wred, 2, cm);
+    }
+    if constexpr (PREC != EM_PREC_FP64) block_max(wred, 3, mkey(f_to_double(xl)));
+    block_max(wred, 4, nf ? 1u : 0u);
+    __syncthreads();
 
     // ---- element extent: Lx bounds every coordinate difference along an edge
     // from local node 0 of a tile element; every face vector, volume and
@@ -779,49 +727,6 @@ __device__ __forceinline__ SScales tile_body(const SArgs& A, int t, const ElemCo
         __syncthreads();
     }
 
-    return SScales{sg_e, sg_v, sg_b, sg_g, range_bad, poison};
-}
-
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void tile_output(const SArgs& A, int t, const SScales& S, char* smem) {
-    using F = Form<PREC>;
-    using FX = Fix<PREC>;
-    using C = typename F::C;
-    using V = typename F::V;
-    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
-    const STile ti = plan_at<STile>(A.plan, H->off_stiles)[t];
-    const ElemConn* conn = plan_at<ElemConn>(A.plan, H->off_sconn) + ti.elem_off;
-    const ElemEdges* tedge = plan_at<ElemEdges>(A.plan, H->off_stedge) + ti.elem_off;
-    const int32_t* halo = plan_at<int32_t>(A.plan, H->off_shalo) + ti.halo_off;
-    const int32_t* hedge = plan_at<int32_t>(A.plan, H->off_shedge) + ti.hedge_off;
-    const int32_t* hbo = plan_at<int32_t>(A.plan, H->off_shbo) + ti.hbo_off;
-    const SFace* sbf = plan_at<SFace>(A.plan, H->off_sbf) + ti.bf_off;
-
-    const SmemS L = s_layout<DIM, PREC, WHAT>(A.D);
-    C* xs = reinterpret_cast<C*>(smem + L.xs);
-    V* ws = reinterpret_cast<V*>(smem + L.ws);
-    V* cs = reinterpret_cast<V*>(smem + L.cs);
-    constexpr int NL = FX::NL;
-    int* acc_e = reinterpret_cast<int*>(smem + L.acc_e);
-    int* acc_v = reinterpret_cast<int*>(smem + L.acc_v);
-    int* acc_g = reinterpret_cast<int*>(smem + L.acc_g);
-    int* acc_b = reinterpret_cast<int*>(smem + L.acc_b);
-    // limb plane strides
-    const int se = DIM * A.D.max_edges, sv = A.D.max_nodes, sgs = DIM * A.D.max_nodes, sb = DIM * A.D.max_bnodes;
-    unsigned* red = reinterpret_cast<unsigned*>(smem + L.red);
-    unsigned* wred = red + 16;
-    static_assert(NTH / 32 <= RED_WARPS, "one maximum slot per warp");
-
-    const int tid = threadIdx.x;
-    const int nnodes = ti.n_own + ti.n_halo;
-    const int nedges = ti.n_eo + ti.n_hedge;
-    const int nbn = ti.n_bo + ti.n_hbo;
-    (void)conn; (void)tedge; (void)halo; (void)hedge; (void)hbo; (void)sbf; (void)xs; (void)ws; (void)cs;
-    (void)red; (void)wred;
-    constexpr int MARK = -2147483647 - 1;
-    const int sg_e = S.sg_e, sg_v = S.sg_v, sg_b = S.sg_b, sg_g = S.sg_g;
-    const bool range_bad = S.range_bad, poison = S.poison;
-
     // ---- outputs: owned targets, records of halo targets ---------------------
     const double esc = DIM == 3 ? 1.0 / 12.0 : 1.0 / 3.0;
     const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
@@ -858,165 +763,6 @@ __device__ __forceinline__ void tile_output(const SArgs& A, int t, const SScales
             else A.rec_n[(int64_t(ti.halo_off) + i - ti.n_own) * REC_DOUBLES + 1 + d] = v;
         }
     }
-}
-
-// one tile, phases in order (one-tile launches and the batched pass)
-template <int DIM, int PREC, int WHAT, int NTH, class PF>
-__device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, const PF& pf) {
-    SStage<DIM, PREC, WHAT, NTH> R;
-    stage_issue<DIM, PREC, WHAT, NTH>(A, t, R);
-    stage_commit<DIM, PREC, WHAT, NTH>(A, t, R, smem);
-    __syncthreads();
-    const SScales S = tile_body<DIM, PREC, WHAT, NTH, SStage<DIM, PREC, WHAT, NTH>::HOIST>(A, t, R.ecb, smem, pf);
-    tile_output<DIM, PREC, WHAT, NTH>(A, t, S, smem);
-}
-
-// ---- asynchronous staging (persistent path, FP64 and DW forms) ---------------
-// The staging gathers of a tile are copied by cp.async straight into the
-// staging buffers as raw doubles (no registers held), and converted in place
-// later by the thread that copied them (its own cp.async writes are visible
-// to it after the wait).  Both forms stage 8-byte values, so a raw double and
-// its converted value occupy the same slot.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"((unsigned long long)__cvta_generic_to_global(src))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void stage_async(const SArgs& A, int t, char* smem) {
-    static_assert(PREC != EM_PREC_MIXED, "the MIXED form stages 4-byte values");
-    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
-    const STile ti = plan_at<STile>(A.plan, H->off_stiles)[t];
-    const int32_t* halo = plan_at<int32_t>(A.plan, H->off_shalo) + ti.halo_off;
-    const int32_t* hedge = plan_at<int32_t>(A.plan, H->off_shedge) + ti.hedge_off;
-    const SmemS L = s_layout<DIM, PREC, WHAT>(A.D);
-    double* xr = reinterpret_cast<double*>(smem + L.xs);
-    double* wr = reinterpret_cast<double*>(smem + L.ws);
-    double* cr = reinterpret_cast<double*>(smem + L.cs);
-    const int tid = threadIdx.x;
-    constexpr bool ADJ = (WHAT & DO_ADJ) != 0;
-    constexpr int HB = 8;   // halo indices requested per thread at a time
-    // halo indices first (the only dependent loads), then the owned rows
-    int hv[HB], he[HB];
-#pragma unroll
-    for (int u = 0; u < HB; u++) {
-        const int i = tid + u * NTH;
-        hv[u] = i < ti.n_halo ? halo[i] : -1;
-        he[u] = (ADJ && i < ti.n_hedge) ? hedge[i] : -1;
-    }
-    for (int i = tid; i < ti.n_own; i += NTH) {
-#pragma unroll
-        for (int d = 0; d < DIM; d++) cp_async8(xr + i * DIM + d, A.x + (int64_t(ti.node0) + i) * DIM + d);
-        if (ADJ) {
-            if (A.c) cp_async8(cr + i, A.c + ti.node0 + i);
-            else cr[i] = 0.0;
-        }
-    }
-    if (ADJ)
-        for (int i = tid; i < ti.n_eo; i += NTH)
-#pragma unroll
-            for (int d = 0; d < DIM; d++) cp_async8(wr + i * DIM + d, A.w + (int64_t(ti.edge0) + i) * DIM + d);
-    for (int i0 = 0; i0 < ti.n_halo || (ADJ && i0 < ti.n_hedge); i0 += HB * NTH) {
-        if (i0 > 0) {
-#pragma unroll
-            for (int u = 0; u < HB; u++) {
-                const int i = i0 + tid + u * NTH;
-                hv[u] = i < ti.n_halo ? halo[i] : -1;
-                he[u] = (ADJ && i < ti.n_hedge) ? hedge[i] : -1;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < HB; u++) {
-            const int i = i0 + tid + u * NTH;
-            if (hv[u] >= 0) {
-                const int k = ti.n_own + i;
-#pragma unroll
-                for (int d = 0; d < DIM; d++) cp_async8(xr + k * DIM + d, A.x + int64_t(hv[u]) * DIM + d);
-                if (ADJ) {
-                    if (A.c) cp_async8(cr + k, A.c + hv[u]);
-                    else cr[k] = 0.0;
-                }
-            }
-            if (ADJ && he[u] >= 0) {
-                const int k = ti.n_eo + i;
-#pragma unroll
-                for (int d = 0; d < DIM; d++) cp_async8(wr + k * DIM + d, A.w + int64_t(he[u]) * DIM + d);
-            }
-        }
-    }
-    cp_async_commit();
-}
-
-// converts, in place, the entries this thread copied in stage_async (same
-// index pattern), and records the staged magnitudes
-template <int DIM, int PREC, int WHAT, int NTH>
-__device__ __forceinline__ void stage_finish(const SArgs& A, int t, char* smem) {
-    using F = Form<PREC>;
-    using FX = Fix<PREC>;
-    using C = typename F::C;
-    using V = typename F::V;
-    static_assert(sizeof(C) == 8 && sizeof(V) == 8, "in-place conversion needs 8-byte staged values");
-    const PlanHeader* H = static_cast<const PlanHeader*>(A.plan);
-    const STile ti = plan_at<STile>(A.plan, H->off_stiles)[t];
-    const SmemS L = s_layout<DIM, PREC, WHAT>(A.D);
-    double* xr = reinterpret_cast<double*>(smem + L.xs);
-    double* wr = reinterpret_cast<double*>(smem + L.ws);
-    double* cr = reinterpret_cast<double*>(smem + L.cs);
-    C* xs = reinterpret_cast<C*>(smem + L.xs);
-    V* ws = reinterpret_cast<V*>(smem + L.ws);
-    V* cs = reinterpret_cast<V*>(smem + L.cs);
-    unsigned* wred = reinterpret_cast<unsigned*>(smem + L.red) + 16;
-    const int tid = threadIdx.x;
-    constexpr bool ADJ = (WHAT & DO_ADJ) != 0;
-    double org[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; d++) {
-        org[d] = A.x[int64_t(ti.node0) * DIM + d];
-        if (!isfinite(org[d])) org[d] = tile_origin_component<DIM>(A.x, ti.node0, ti.n_own, d);
-    }
-    cp_async_wait_all();
-    unsigned wm = 0u, cm = 0u;
-    float xl = 0.f;
-    bool nf = false;
-    auto node = [&](int k) {
-#pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            const C xc = finite_or_nan(F::coord(xr[k * DIM + d], org[d]));
-            xs[k * DIM + d] = xc;
-            nf |= is_nan(xc);
-            if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
-        }
-        if (ADJ) {
-            const V c1 = finite_or_nan(F::from_double(cr[k]));
-            cs[k] = c1;
-            nf |= is_nan(c1);
-            cm = max(cm, FX::mag(c1));
-        }
-    };
-    auto edge = [&](int k) {
-#pragma unroll
-        for (int d = 0; d < DIM; d++) {
-            const V w1 = finite_or_nan(F::from_double(wr[k * DIM + d]));
-            ws[k * DIM + d] = w1;
-            nf |= is_nan(w1);
-            wm = max(wm, FX::mag(w1));
-        }
-    };
-    for (int i = tid; i < ti.n_own; i += NTH) node(i);
-    for (int i = tid; i < ti.n_halo; i += NTH) node(ti.n_own + i);
-    if (ADJ) {
-        for (int i = tid; i < ti.n_eo; i += NTH) edge(i);
-        for (int i = tid; i < ti.n_hedge; i += NTH) edge(ti.n_eo + i);
-    }
-    if (ADJ) {
-        block_max(wred, 1, wm);
-        block_max(wred, 2, cm);
-    }
-    if constexpr (PREC != EM_PREC_FP64) block_max(wred, 3, mkey(f_to_double(xl)));
-    block_max(wred, 4, nf ? 1u : 0u);
 }
 
 // ---- merge: records into the owners' outputs ---------------------------------
@@ -1117,35 +863,6 @@ __global__ void __launch_bounds__(NTH, NTH == NT ? scatter_min_ctas<PREC, WHAT>(
     run_stile<DIM, PREC, WHAT, NTH>(A, t, smem, pf);
 }
 
-// Persistent form: a fixed grid of CTAs (resident CTAs per SM x SMs), CTA b
-// runs tiles b, b + gridDim.x, ... (the order the hardware dispatches one CTA
-// per tile).  Each tile's successor is staged while the tile writes its
-// outputs; no CTA waits on another.  Results are those of k_stile.
-template <int DIM, int PREC, int WHAT, int NTH>
-__global__ void __launch_bounds__(NTH, NTH == NT ? scatter_min_ctas<PREC, WHAT>() : 1) k_stile_p(SArgs A) {
-    extern __shared__ __align__(16) char smem[];
-    const int64_t n = A.n_tiles, step = gridDim.x;
-    int64_t t = blockIdx.x;
-    if (t >= n) return;
-    stage_async<DIM, PREC, WHAT, NTH>(A, (int)t, smem);
-    stage_finish<DIM, PREC, WHAT, NTH>(A, (int)t, smem);
-    for (;;) {
-        __syncthreads();   // staged data visible; the previous tile's output pass is done with the accumulators
-        const int64_t tn = t + step;
-        auto pf = [&](int lane) {
-            if (A.ahead > 0 && tn < n) prefetch_stile_l2<DIM, (WHAT & DO_ADJ) != 0>(A, (int)tn, lane);
-        };
-        const SScales S = tile_body<DIM, PREC, WHAT, NTH, false>(A, (int)t, nullptr, smem, pf);
-        // the staging buffers are free (the last barrier of tile_body follows
-        // their last reads); the accumulators are read by the output pass
-        if (tn < n) stage_async<DIM, PREC, WHAT, NTH>(A, (int)tn, smem);
-        tile_output<DIM, PREC, WHAT, NTH>(A, (int)t, S, smem);
-        if (tn >= n) break;
-        stage_finish<DIM, PREC, WHAT, NTH>(A, (int)tn, smem);
-        t = tn;
-    }
-}
-
 inline int check_valence(int val_e, int val_v) {
     // A limb plane entry holds the sum of fewer than 1024 limbs of magnitude
     // <= 2^21.  Per element an edge entry receives up to 3 of them (the
@@ -1160,9 +877,6 @@ inline int check_valence(int val_e, int val_v) {
 
 template <int DIM, int PREC, int WHAT>
 int launch_stiles(const em_mesh* m, SArgs& A, cudaStream_t s) {
-    // FP64 and DW tiles run on the persistent grid with asynchronous staging;
-    // the MIXED form (4-byte staged values) launches one CTA per tile
-    constexpr bool PERSIST = PREC != EM_PREC_MIXED;
     const SmemS L = s_layout<DIM, PREC, WHAT>(A.D);
     static size_t configured = 0;
     EM_TRY(check_valence(A.val_e, A.val_v));
@@ -1172,16 +886,9 @@ int launch_stiles(const em_mesh* m, SArgs& A, cudaStream_t s) {
     if (L.total > 48 * 1024 && L.total > configured) {
         EM_CUDA_TRY(cudaFuncSetAttribute(k_stile<DIM, PREC, WHAT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024));
-        if constexpr (PERSIST)
-            EM_CUDA_TRY(cudaFuncSetAttribute(k_stile_p<DIM, PREC, WHAT, NT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        if constexpr (DIM == 3) {
+        if constexpr (DIM == 3)
             EM_CUDA_TRY(cudaFuncSetAttribute(k_stile<DIM, PREC, WHAT, 2 * NT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-            if constexpr (PERSIST)
-                EM_CUDA_TRY(cudaFuncSetAttribute(k_stile_p<DIM, PREC, WHAT, 2 * NT>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        }
         configured = 227 * 1024;
     }
     // one resident CTA of NT threads per SM leaves half the register file
@@ -1189,55 +896,31 @@ int launch_stiles(const em_mesh* m, SArgs& A, cudaStream_t s) {
     // on the thread count)
     bool wide = false;
     int per_sm = 0;
-    auto occupancy = [&](auto kernel, int threads) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, L.total);
-    };
-    if constexpr (PERSIST) EM_CUDA_TRY(occupancy(k_stile_p<DIM, PREC, WHAT, NT>, NT));
-    else EM_CUDA_TRY(occupancy(k_stile<DIM, PREC, WHAT, NT>, NT));
+    EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stile<DIM, PREC, WHAT, NT>, NT, L.total));
     if constexpr (DIM == 3) {
         if (per_sm < 2) {
             wide = true;
-            if constexpr (PERSIST) EM_CUDA_TRY(occupancy(k_stile_p<DIM, PREC, WHAT, 2 * NT>, 2 * NT));
-            else EM_CUDA_TRY(occupancy(k_stile<DIM, PREC, WHAT, 2 * NT>, 2 * NT));
+            EM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stile<DIM, PREC, WHAT, 2 * NT>,
+                                                                      2 * NT, L.total));
         }
     }
+    // with one CTA per SM nothing hides a tile's staging latency: tile t
+    // prefetches the tile that starts after it (tiles resident at once ahead)
+    A.ahead = per_sm == 1 ? num_sms() : 0;
     const int64_t n_tiles = A.n_tiles;
-    if constexpr (PERSIST) {
-        // with one CTA per SM nothing else hides a tile's latency: each tile
-        // prefetches its successor on the same CTA into L2
-        A.ahead = per_sm == 1 ? 1 : 0;
-        // persistent grid: the resident CTAs, each staging its next tile while
-        // it writes the current one's outputs
-        const int64_t resident = int64_t(num_sms()) * (per_sm > 0 ? per_sm : 1);
-        const unsigned grid = (unsigned)(n_tiles < resident ? n_tiles : resident);
-        A.tile_base = 0;
+    const int64_t chunk = 1 << 30;
+    for (int64_t base = 0; base < n_tiles; base += chunk) {
+        A.tile_base = base;
+        const int64_t nb = n_tiles - base < chunk ? n_tiles - base : chunk;
         if constexpr (DIM == 3) {
             if (wide)
-                k_stile_p<DIM, PREC, WHAT, 2 * NT><<<grid, 2 * NT, L.total, s>>>(A);
+                k_stile<DIM, PREC, WHAT, 2 * NT><<<(unsigned)nb, 2 * NT, L.total, s>>>(A);
             else
-                k_stile_p<DIM, PREC, WHAT, NT><<<grid, NT, L.total, s>>>(A);
+                k_stile<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
         } else {
-            k_stile_p<DIM, PREC, WHAT, NT><<<grid, NT, L.total, s>>>(A);
+            k_stile<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
         }
         note_launches(1);
-    } else {
-        // one CTA per tile; with one CTA per SM, tile t prefetches the tile
-        // that starts after it (tiles resident at once ahead)
-        A.ahead = per_sm == 1 ? num_sms() : 0;
-        const int64_t chunk = 1 << 30;
-        for (int64_t base = 0; base < n_tiles; base += chunk) {
-            A.tile_base = base;
-            const int64_t nb = n_tiles - base < chunk ? n_tiles - base : chunk;
-            if constexpr (DIM == 3) {
-                if (wide)
-                    k_stile<DIM, PREC, WHAT, 2 * NT><<<(unsigned)nb, 2 * NT, L.total, s>>>(A);
-                else
-                    k_stile<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
-            } else {
-                k_stile<DIM, PREC, WHAT, NT><<<(unsigned)nb, NT, L.total, s>>>(A);
-            }
-            note_launches(1);
-        }
     }
     // merge the records (none on a grid that fits one tile)
     const int64_t nmerge = m->plan_info[EM_PLAN_INFO_REC_EDGES] + m->plan_info[EM_PLAN_INFO_REC_NODES] +
