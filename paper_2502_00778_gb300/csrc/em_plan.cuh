@@ -93,7 +93,8 @@ static_assert(sizeof(STile) == 64, "STile is 64 bytes");
 struct SFace { uint16_t v[3]; uint16_t e[3]; uint16_t b[3]; uint16_t pad[3]; };
 static_assert(sizeof(SFace) == 24, "SFace is 24 bytes");
 
-// records: 4 doubles each (edges: n; nodes: V, grad; boundary nodes: bnormal)
+// records: at most 4 doubles each (edges: n; nodes: V, grad; boundary nodes:
+// bnormal), the bound that sizes a grid's record buffer
 constexpr int REC_DOUBLES = 4;
 
 template <typename T>

@@ -73,9 +73,10 @@ struct SArgs {
     double* vol;
     double* bnormal;
     double* grad;
-    double* rec_e;          // [edge records][4]: n
-    double* rec_n;          // [node records][4]: V, grad
-    double* rec_b;          // [boundary-node records][4]: bnormal
+    double* rec_e;          // [edge records][DIM]: n
+    double* rec_v;          // [node records]: V
+    double* rec_g;          // [node records][DIM]: grad
+    double* rec_b;          // [boundary-node records][DIM]: bnormal
     SDims D;
     int n_tiles;
     int val_e, val_v;       // largest edge / node valence of the grid
@@ -736,33 +737,38 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
         if (range_bad || (poison && p[q] == MARK)) return qnan_d();
         return FX::out(acc_load<NL>(p, stride, q), sg, sc);
     };
+    // Every output loop takes U entries per thread at a time, so that U
+    // independent conversions are in flight.  Owned entries go to the outputs,
+    // halo entries to this tile's contiguous block of records (packed:
+    // edges and boundary nodes DIM doubles, nodes V then DIM gradient doubles
+    // in separate arrays).
+    constexpr int U = 4;
+    auto emit = [&](int N, const int* p, int stride, int sg, double sc, int n_own_q, double* own, double* rec) {
+        for (int q0 = tid; q0 < N; q0 += U * NTH) {
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int q = q0 + u * NTH;
+                v[u] = q < N ? outv(p, stride, q, sg, sc) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int q = q0 + u * NTH;
+                if (q < n_own_q) own[q] = v[u];
+                else if (q < N) rec[q - n_own_q] = v[u];
+            }
+        }
+    };
     if (WHAT & DO_FWD) {
-        for (int q = tid; q < nedges * DIM; q += NTH) {
-            const int i = q / DIM, d = q - i * DIM;
-            const double v = outv(acc_e, se, q, sg_e, esc);
-            if (i < ti.n_eo) A.n_out[int64_t(ti.edge0) * DIM + q] = v;
-            else A.rec_e[(int64_t(ti.hedge_off) + i - ti.n_eo) * REC_DOUBLES + d] = v;
-        }
-        for (int q = tid; q < nbn * DIM; q += NTH) {
-            const int i = q / DIM, d = q - i * DIM;
-            const double v = outv(acc_b, sb, q, sg_b, bsc);
-            if (i < ti.n_bo) A.bnormal[int64_t(ti.bnode0) * DIM + q] = v;
-            else A.rec_b[(int64_t(ti.hbo_off) + i - ti.n_bo) * REC_DOUBLES + d] = v;
-        }
-        for (int i = tid; i < nnodes; i += NTH) {
-            const double v = outv(acc_v, sv, i, sg_v, vsc);
-            if (i < ti.n_own) A.vol[int64_t(ti.node0) + i] = v;
-            else A.rec_n[(int64_t(ti.halo_off) + i - ti.n_own) * REC_DOUBLES] = v;
-        }
+        emit(nedges * DIM, acc_e, se, sg_e, esc, ti.n_eo * DIM, A.n_out + int64_t(ti.edge0) * DIM,
+             A.rec_e + int64_t(ti.hedge_off) * DIM);
+        emit(nbn * DIM, acc_b, sb, sg_b, bsc, ti.n_bo * DIM, A.bnormal + int64_t(ti.bnode0) * DIM,
+             A.rec_b + int64_t(ti.hbo_off) * DIM);
+        emit(nnodes, acc_v, sv, sg_v, vsc, ti.n_own, A.vol + ti.node0, A.rec_v + ti.halo_off);
     }
-    if (WHAT & DO_ADJ) {
-        for (int q = tid; q < nnodes * DIM; q += NTH) {
-            const int i = q / DIM, d = q - i * DIM;
-            const double v = outv(acc_g, sgs, q, sg_g, DIM == 3 ? 1.0 / 12.0 : 1.0);
-            if (i < ti.n_own) A.grad[int64_t(ti.node0) * DIM + q] = v;
-            else A.rec_n[(int64_t(ti.halo_off) + i - ti.n_own) * REC_DOUBLES + 1 + d] = v;
-        }
-    }
+    if (WHAT & DO_ADJ)
+        emit(nnodes * DIM, acc_g, sgs, sg_g, DIM == 3 ? 1.0 / 12.0 : 1.0, ti.n_own * DIM,
+             A.grad + int64_t(ti.node0) * DIM, A.rec_g + int64_t(ti.halo_off) * DIM);
 }
 
 // ---- merge: records into the owners' outputs ---------------------------------
@@ -776,7 +782,8 @@ struct MergeArgs {
     double* bnormal;
     double* grad;
     const double* rec_e;
-    const double* rec_n;
+    const double* rec_v;
+    const double* rec_g;
     const double* rec_b;
 };
 
@@ -800,7 +807,7 @@ __device__ __forceinline__ void merge_targets(const MergeArgs& M, int64_t first,
 #pragma unroll
             for (int d = 0; d < DIM; d++) v[d] = M.n_out[e * DIM + d];
             for (int r = me_ptr[k]; r < me_ptr[k + 1]; r++) {
-                const double* p = M.rec_e + int64_t(me_rec[r]) * REC_DOUBLES;
+                const double* p = M.rec_e + int64_t(me_rec[r]) * DIM;
 #pragma unroll
                 for (int d = 0; d < DIM; d++) v[d] = __dadd_rn(v[d], p[d]);
             }
@@ -814,11 +821,11 @@ __device__ __forceinline__ void merge_targets(const MergeArgs& M, int64_t first,
 #pragma unroll
                 for (int d = 0; d < DIM; d++) g[d] = M.grad[i * DIM + d];
             for (int r = mn_ptr[j]; r < mn_ptr[j + 1]; r++) {
-                const double* p = M.rec_n + int64_t(mn_rec[r]) * REC_DOUBLES;
-                if (WHAT & DO_FWD) v = __dadd_rn(v, p[0]);
+                const int64_t rr = mn_rec[r];
+                if (WHAT & DO_FWD) v = __dadd_rn(v, M.rec_v[rr]);
                 if (WHAT & DO_ADJ)
 #pragma unroll
-                    for (int d = 0; d < DIM; d++) g[d] = __dadd_rn(g[d], p[1 + d]);
+                    for (int d = 0; d < DIM; d++) g[d] = __dadd_rn(g[d], M.rec_g[rr * DIM + d]);
             }
             if (WHAT & DO_FWD) M.vol[i] = v;
             if (WHAT & DO_ADJ)
@@ -830,7 +837,7 @@ __device__ __forceinline__ void merge_targets(const MergeArgs& M, int64_t first,
 #pragma unroll
             for (int d = 0; d < DIM; d++) v[d] = M.bnormal[b * DIM + d];
             for (int r = mb_ptr[j]; r < mb_ptr[j + 1]; r++) {
-                const double* p = M.rec_b + int64_t(mb_rec[r]) * REC_DOUBLES;
+                const double* p = M.rec_b + int64_t(mb_rec[r]) * DIM;
 #pragma unroll
                 for (int d = 0; d < DIM; d++) v[d] = __dadd_rn(v[d], p[d]);
             }
@@ -926,7 +933,7 @@ int launch_stiles(const em_mesh* m, SArgs& A, cudaStream_t s) {
     const int64_t nmerge = m->plan_info[EM_PLAN_INFO_REC_EDGES] + m->plan_info[EM_PLAN_INFO_REC_NODES] +
                            m->plan_info[EM_PLAN_INFO_REC_BNODES];
     if (nmerge > 0) {
-        MergeArgs M{A.plan, A.n_out, A.vol, A.bnormal, A.grad, A.rec_e, A.rec_n, A.rec_b};
+        MergeArgs M{A.plan, A.n_out, A.vol, A.bnormal, A.grad, A.rec_e, A.rec_v, A.rec_g, A.rec_b};
         k_merge<DIM, WHAT><<<grid_for(nmerge, NT), NT, 0, s>>>(M);
         note_launches(1);
     }
@@ -941,17 +948,25 @@ int dispatch_s(const em_mesh* m, int what, SArgs& A, cudaStream_t s) {
     return launch_stiles<DIM, PREC, DO_FWD | DO_ADJ>(m, A, s);
 }
 
-// records of one grid in a buffer of scatter_rec_bytes(plan_info) bytes
+// records of one grid in a buffer of scatter_rec_bytes(plan_info) bytes (an
+// upper bound for both dimensions: 4 doubles per record), packed as
+// [edge records][DIM], [node records] (V), [node records][DIM] (grad),
+// [boundary-node records][DIM]
 inline size_t scatter_rec_bytes(const int64_t* pi) {
     return sizeof(double) * REC_DOUBLES *
            (size_t)(pi[EM_PLAN_INFO_REC_EDGES] + pi[EM_PLAN_INFO_REC_NODES] + pi[EM_PLAN_INFO_REC_BNODES]);
 }
 
-__host__ __device__ inline void rec_pointers(const int64_t* pi, void* base, double** re, double** rn, double** rb) {
+__host__ __device__ inline void rec_pointers(const int64_t* pi, int dim, void* base, double** re, double** rv,
+                                             double** rg, double** rb) {
     double* p = static_cast<double*>(base);
     *re = p;
-    *rn = p + REC_DOUBLES * pi[EM_PLAN_INFO_REC_EDGES];
-    *rb = *rn + REC_DOUBLES * pi[EM_PLAN_INFO_REC_NODES];
+    p += dim * pi[EM_PLAN_INFO_REC_EDGES];
+    *rv = p;
+    p += pi[EM_PLAN_INFO_REC_NODES];
+    *rg = p;
+    p += dim * pi[EM_PLAN_INFO_REC_NODES];
+    *rb = p;
 }
 
 // ---- batched: the tiles of many grids in one launch --------------------------
@@ -966,7 +981,7 @@ __device__ __forceinline__ void args_from_item(const em_batch_item& it, SArgs& A
     A.plan = it.mesh.plan;
     A.x = it.x; A.w = it.w; A.c = it.c;
     A.n_out = it.n_edge; A.vol = it.vol; A.bnormal = it.bnormal; A.grad = it.grad_x;
-    rec_pointers(it.mesh.plan_info, it.rec, &A.rec_e, &A.rec_n, &A.rec_b);
+    rec_pointers(it.mesh.plan_info, it.mesh.dim, it.rec, &A.rec_e, &A.rec_v, &A.rec_g, &A.rec_b);
     A.n_tiles = (int)it.mesh.plan_info[EM_PLAN_INFO_TILES];
     A.val_e = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_EDGE_VALENCE];
     A.val_v = (int)it.mesh.plan_info[EM_PLAN_INFO_MAX_NODE_VALENCE];
@@ -1074,9 +1089,9 @@ __global__ void __launch_bounds__(NT) k_sbatched_merge(const em_batch_item* __re
     MergeArgs M;
     M.plan = it.mesh.plan;
     M.n_out = it.n_edge; M.vol = it.vol; M.bnormal = it.bnormal; M.grad = it.grad_x;
-    double *re, *rn, *rb;
-    rec_pointers(it.mesh.plan_info, it.rec, &re, &rn, &rb);
-    M.rec_e = re; M.rec_n = rn; M.rec_b = rb;
+    double *re, *rv, *rg, *rb;
+    rec_pointers(it.mesh.plan_info, DIM, it.rec, &re, &rv, &rg, &rb);
+    M.rec_e = re; M.rec_v = rv; M.rec_g = rg; M.rec_b = rb;
     merge_targets<DIM, DO_FWD | DO_ADJ>(M, blockIdx.x * int64_t(NT) + threadIdx.x, int64_t(gridDim.x) * NT);
 }
 
@@ -1151,7 +1166,7 @@ int scatter_run(const em_mesh* m, int prec, int what, const double* x, const dou
     A.plan = m->plan;
     A.x = x; A.w = w; A.c = c;
     A.n_out = n; A.vol = vol; A.bnormal = bnormal; A.grad = g;
-    rec_pointers(pi, ws, &A.rec_e, &A.rec_n, &A.rec_b);
+    rec_pointers(pi, m->dim, ws, &A.rec_e, &A.rec_v, &A.rec_g, &A.rec_b);
     A.D.max_nodes = (int)pi[EM_PLAN_INFO_S_MAX_NODES];
     A.D.max_edges = (int)pi[EM_PLAN_INFO_S_MAX_EDGES];
     A.D.max_bnodes = (int)std::max<int64_t>(pi[EM_PLAN_INFO_S_MAX_BNODES], 1);
