@@ -729,16 +729,13 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     }
 
     // ---- outputs: owned targets, records of halo targets ---------------------
-    // output factors 2^-k / 3 (or 2^-k): 3D edges 1/12, volumes 1/24, boundary
-    // normals 1/3, gradients 1/12 (the 3D sums hold 12 g); 2D edges 1/3,
-    // volumes 1/6, boundary normals 1/2, gradients 1
-    constexpr int ke = DIM == 3 ? 2 : 0, kv = DIM == 3 ? 3 : 1, kb = DIM == 3 ? 0 : 1, kg = DIM == 3 ? 2 : 0;
-    constexpr bool b3 = DIM == 3, g3 = DIM == 3;
-    // out(p, q): entry q of the planes p times 2^-sg (/ 3 when div3), NaN where marked
-    auto outv = [&](const int* p, int stride, int q, int sg, bool div3) {
+    const double esc = DIM == 3 ? 1.0 / 12.0 : 1.0 / 3.0;
+    const double vsc = DIM == 3 ? 1.0 / 24.0 : 1.0 / 6.0;
+    const double bsc = DIM == 3 ? 1.0 / 3.0 : 1.0 / 2.0;
+    // out(p, q): entry q of the planes p at scale sg, NaN where marked
+    auto outv = [&](const int* p, int stride, int q, int sg, double sc) {
         if (range_bad || (poison && p[q] == MARK)) return qnan_d();
-        const long long v = acc_load<NL>(p, stride, q);
-        return div3 ? fx_to_double_div3(v, sg) : fx_to_double(v, sg);
+        return FX::out(acc_load<NL>(p, stride, q), sg, sc);
     };
     // Every output loop takes U entries per thread at a time, so that U
     // independent conversions are in flight.  Owned entries go to the outputs,
@@ -746,13 +743,13 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     // edges and boundary nodes DIM doubles, nodes V then DIM gradient doubles
     // in separate arrays).
     constexpr int U = 4;
-    auto emit = [&](int N, const int* p, int stride, int sg, bool div3, int n_own_q, double* own, double* rec) {
+    auto emit = [&](int N, const int* p, int stride, int sg, double sc, int n_own_q, double* own, double* rec) {
         for (int q0 = tid; q0 < N; q0 += U * NTH) {
             double v[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int q = q0 + u * NTH;
-                v[u] = q < N ? outv(p, stride, q, sg, div3) : 0.0;
+                v[u] = q < N ? outv(p, stride, q, sg, sc) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
@@ -763,15 +760,15 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
         }
     };
     if (WHAT & DO_FWD) {
-        emit(nedges * DIM, acc_e, se, sg_e + ke, true, ti.n_eo * DIM, A.n_out + int64_t(ti.edge0) * DIM,
+        emit(nedges * DIM, acc_e, se, sg_e, esc, ti.n_eo * DIM, A.n_out + int64_t(ti.edge0) * DIM,
              A.rec_e + int64_t(ti.hedge_off) * DIM);
-        emit(nbn * DIM, acc_b, sb, sg_b + kb, b3, ti.n_bo * DIM, A.bnormal + int64_t(ti.bnode0) * DIM,
+        emit(nbn * DIM, acc_b, sb, sg_b, bsc, ti.n_bo * DIM, A.bnormal + int64_t(ti.bnode0) * DIM,
              A.rec_b + int64_t(ti.hbo_off) * DIM);
-        emit(nnodes, acc_v, sv, sg_v + kv, true, ti.n_own, A.vol + ti.node0, A.rec_v + ti.halo_off);
+        emit(nnodes, acc_v, sv, sg_v, vsc, ti.n_own, A.vol + ti.node0, A.rec_v + ti.halo_off);
     }
     if (WHAT & DO_ADJ)
-        emit(nnodes * DIM, acc_g, sgs, sg_g + kg, g3, ti.n_own * DIM, A.grad + int64_t(ti.node0) * DIM,
-             A.rec_g + int64_t(ti.halo_off) * DIM);
+        emit(nnodes * DIM, acc_g, sgs, sg_g, DIM == 3 ? 1.0 / 12.0 : 1.0, ti.n_own * DIM,
+             A.grad + int64_t(ti.node0) * DIM, A.rec_g + int64_t(ti.halo_off) * DIM);
 }
 
 // ---- merge: records into the owners' outputs ---------------------------------

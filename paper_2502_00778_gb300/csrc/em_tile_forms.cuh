@@ -206,29 +206,6 @@ __device__ __forceinline__ double fx_to_double(long long q, int sg) {
     return __longlong_as_double((long long)((((unsigned long long)(field - 1)) << 52) + m + sign));
 }
 
-// q / 3 * 2^-sg as a double, rounded to nearest even, integer instructions
-// only: |q| = 3 d + r; d + r/3 is normalised with the leading bits of r/3
-// (0.0101... for r = 1, 0.1010... for r = 2) shifted in below d, and since the
-// expansion of r/3 never ends when r != 0, a remainder of exactly half the
-// last place then lies above the midpoint.  The output factors 1/12, 1/24,
-// 1/3 and 1/6 are 2^-k / 3, so the outputs need no FP64 multiply.
-__device__ __forceinline__ double fx_to_double_div3(long long q, int sg) {
-    if (q == 0) return 0.0;
-    const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ull;
-    const unsigned long long a = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
-    if (a < 3ull) return __dmul_rn(__ll2double_rn(q), __dmul_rn(pow2d(-sg), 1.0 / 3.0));   // |value| < 2^-sg (rare)
-    const unsigned long long d = a / 3ull;
-    const unsigned r = (unsigned)(a - 3ull * d);
-    const int lz = __clzll((long long)d);   // d < 2^61: lz >= 3
-    const unsigned long long frac = r == 0u ? 0ull : (r == 1u ? 0x5555555555555555ull : 0xAAAAAAAAAAAAAAAAull);
-    const unsigned long long m64 = (d << lz) | (frac >> (64 - lz));
-    unsigned long long m = m64 >> 11;
-    const unsigned rem = (unsigned)(m64 & 0x7ffull);
-    m += (rem > 0x400u || (rem == 0x400u && (r != 0u || (m & 1ull)))) ? 1ull : 0ull;
-    const long long field = 1023 + 63 - lz - sg;
-    return __longlong_as_double((long long)((((unsigned long long)(field - 1)) << 52) + m + sign));
-}
-
 // Magnitudes as order-preserving 32-bit keys: the upper word of |v| as an
 // IEEE double (exponent and 20 mantissa bits).  Non-negative doubles order
 // like their bit patterns, so an integer max gives the max magnitude.  Every
