@@ -146,10 +146,17 @@ struct Lq {
 
 constexpr float FX_MAGIC = 12582912.0f;   // 1.5 * 2^23
 
-__device__ __forceinline__ int fx_round(float t, float& rem) {
-    const float y = __fadd_rn(t, FX_MAGIC);
-    rem = __fsub_rn(t, __fsub_rn(y, FX_MAGIC));
+// round(t*s) for a power of two s (|t*s| < 2^22), as an int, and the exact
+// remainder t*s - round(t*s): t*s is exact, so fma(t, s, MAGIC) rounds it as
+// t*s + MAGIC would, and fma(t, s, -round) is exact (the scaling costs no
+// separate multiply)
+__device__ __forceinline__ int fx_round_s(float t, float s, float& rem) {
+    const float y = __fmaf_rn(t, s, FX_MAGIC);
+    rem = __fmaf_rn(t, s, -__fsub_rn(y, FX_MAGIC));
     return __float_as_int(y) - 0x4B400000;
+}
+__device__ __forceinline__ int fx_round_last(float t, float s) {   // remainder not needed
+    return __float_as_int(__fmaf_rn(t, s, FX_MAGIC)) - 0x4B400000;
 }
 
 // -(a + b + c) and x -= q, limb by limb: exact integer sums of quantised
@@ -244,13 +251,11 @@ struct Fix<EM_PREC_DW> {
     static constexpr int NL = 3, TOP = 62, LO = -80, HI = 148;
     static __device__ __forceinline__ Lq q(dw v, int sg) {
         float r;
-        const float th = __fmul_rn(v.h, pow2f(sg - 42));
-        const int a = fx_round(th, r);
-        const int b = fx_round(__fmul_rn(r, 2097152.0f), r);
-        const int c = fx_round(__fmul_rn(r, 2097152.0f), r);
-        const float tl = __fmul_rn(v.l, pow2f(sg - 21));
-        const int b2 = fx_round(tl, r);
-        const int c2 = fx_round(__fmul_rn(r, 2097152.0f), r);
+        const int a = fx_round_s(v.h, pow2f(sg - 42), r);
+        const int b = fx_round_s(r, 2097152.0f, r);
+        const int c = fx_round_last(r, 2097152.0f);
+        const int b2 = fx_round_s(v.l, pow2f(sg - 21), r);
+        const int c2 = fx_round_last(r, 2097152.0f);
         return {a, b + b2, c + c2};
     }
     static __device__ __forceinline__ unsigned mag(dw v) {
@@ -268,9 +273,8 @@ struct Fix<EM_PREC_MIXED> {
     static constexpr int NL = 2, TOP = 41, LO = -80, HI = 148;
     static __device__ __forceinline__ Lq q(float v, int sg) {
         float r;
-        const int a = fx_round(__fmul_rn(v, pow2f(sg - 21)), r);
-        const int b = fx_round(__fmul_rn(r, 2097152.0f), r);
-        return {a, b, 0};
+        const int a = fx_round_s(v, pow2f(sg - 21), r);
+        return {a, fx_round_last(r, 2097152.0f), 0};
     }
     static __device__ __forceinline__ unsigned mag(float v) { return mkey(f_to_double(v)); }
     static __device__ __forceinline__ double out(long long q, int sg, double sc) {
