@@ -594,12 +594,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    # three timed runs of ke pipelined steps; the median run is reported (the
+    # five timed runs of ke pipelined steps; the median run is reported (the
     # host side of the copies shares the machine's memory system, so one run
-    # can catch a transient slowdown), all three are listed
+    # can catch a transient slowdown), all five are listed
     ke = max(4, K // 2)
     e2e_runs = []
-    for _ in range(3):
+    for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s_up)
         for k in range(ke):
@@ -609,7 +609,7 @@ def run_ours(args):
         e1.record(s_up)
         torch.cuda.synchronize()
         e2e_runs.append(e0.elapsed_time(e1) / ke)
-    e2e_ms = sorted(e2e_runs)[1]
+    e2e_ms = sorted(e2e_runs)[2]
     # the last step's results arrived on the host: check one of them is filled in
     assert torch.isfinite(hout[(ke - 1) % 2][1][:16]).all()
     if ws > 1:
@@ -733,7 +733,7 @@ def run_ours(args):
                     "ms_per_step": e2e_ms, "ms_per_step_runs": [round(r, 4) for r in e2e_runs],
                     "method": "public API, pinned host buffers, every step uploads x, w, c and downloads n, V, "
                               "bnormal, grad; steps double-buffered over upload / compute / download streams; "
-                              "median of three timed runs"},
+                              "median of five timed runs"},
             "gpu_launches": int(launches),
             "clocks": clk,
             "edge_build_ms": edge_build_ms, "plan_build_ms": plan_build_ms,
