@@ -72,10 +72,29 @@ def test_committed_traffic_matches_its_source():
     carries that file's current checksum (otherwise the benchmark drops it)."""
     j = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     for key, ent in j.items():
+        if key.startswith("_"):      # notes
+            continue
         p = os.path.join(ROOT, ent["source"])
         assert os.path.exists(p), key
         assert hashlib.sha1(open(p, "rb").read()).hexdigest() == ent["source_sha1"], key
         assert ent["dram_bytes_per_launch"] > 0 and ent["scale_to_full"] > 0
+
+
+def test_committed_fp64_counts_match_their_source():
+    """The FP64 instruction counts behind the ALU ceiling of the native-FP64
+    forms: every entry names its kernel's source at the captured checksum, and
+    the benchmark reads them back."""
+    j = json.load(open(os.path.join(ROOT, "profiles", "fp64_ops.json")))
+    kernels = [k for k in j if not k.startswith("_")]
+    assert "k_fwd_atomic3<fp64>" in kernels
+    for key in kernels:
+        ent = j[key]
+        p = os.path.join(ROOT, ent["source"])
+        assert hashlib.sha1(open(p, "rb").read()).hexdigest() == ent["source_sha1"], key
+        per = ent["fp64_pipe_thread_inst"] / ent["elements"]
+        assert abs(per - ent["fp64_ops_per_element"]) < 0.01
+        assert bench.fp64_ops(key) == pytest.approx(ent["fp64_ops_per_element"])
+    assert bench.fp64_peak_ops() == pytest.approx(2 * 152 * 2.07e9)
 
 
 def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
