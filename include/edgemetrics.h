@@ -82,12 +82,15 @@ extern "C" {
                              accumulation; bit-reproducible run to run */
 #define EM_PATH_CSR    2  /* edge-centric CSR gather (per edge, its element slots in
                              ascending order; FP64 only); bit-reproducible */
-#define EM_PATH_TILED  3  /* same tiles as EM_PATH_GATHER, but each tile element adds
-                             its contributions to the tile's accumulators with
+#define EM_PATH_TILED  3  /* scatter tiles over the same node ranges as
+                             EM_PATH_GATHER: every element is computed once, by
+                             the tile of its lowest node, and adds its
+                             contributions to the tile's accumulators with
                              shared-memory integer atomics on exact fixed-point
-                             values (per-tile power-of-two scale, ~2^-49 relative
-                             resolution): fewer instructions and barriers, and
-                             bit-reproducible run to run */
+                             values (per-tile power-of-two scale); partial sums
+                             of targets owned by later tiles are added to the
+                             owners' outputs in a fixed order, so the results
+                             are bit-reproducible run to run */
 
 int em_version(void);
 
@@ -414,8 +417,8 @@ typedef struct em_batch_item {
  * single-grid EM_PATH_TILED pass runs that tile (exact fixed-point
  * accumulation), so every output equals em_edge_metrics_fused(...,
  * EM_PATH_TILED) bit for bit, whatever the launch shape.  No block waits on
- * another block.  Grids with an edge valence above 1000 or a node valence
- * above 250 are refused (EM_ERR_ARG), as in the tiled path.
+ * another block.  Grids with an edge valence above 340 or a node valence
+ * above 170 are refused (EM_ERR_ARG), as in the tiled path.
  *   items        DEVICE array [n_meshes] of em_batch_item (pointers inside
  *                are device pointers); all grids must have the same dim.
  *   tile_prefix  DEVICE int64 [n_meshes+1]: exclusive prefix sum of the grids'
