@@ -224,89 +224,84 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     }
 
     // ---- stage coordinates (and w, c) and find the tile's magnitudes --------
-    // The staged arrays are copied flat: entry f of the coordinates is
-    // component f % DIM of local node f / DIM (w likewise per local edge), so
-    // consecutive threads read consecutive doubles of the owned rows (one
-    // contiguous block) and neighbouring lanes the DIM doubles of a halo row.
-    // Each round a thread takes SBX coordinate, SBC node-weight and SBW edge-
-    // weight entries: it requests the halo indices of all of them first, then
-    // all their values, and converts last (two dependent trips to memory per
-    // round).  The tile origin is loaded with the indices and only replaced
-    // when it is not finite (rare).
-    constexpr int SBX = 3, SBC = 1, SBW = (WHAT & DO_ADJ) ? 8 : 1;
+    // Each thread takes up to SB nodes and SBW edges per round.  It first
+    // requests the halo indices of all of them (owned rows need none), then all
+    // their gathers, and converts last, so a round costs two dependent trips to
+    // L2 / HBM however many lists it covers.  The tile origin is loaded with
+    // the indices and only replaced when it is not finite (rare).
+    constexpr int SB = NTH > NT ? 1 : 2, SBW = (WHAT & DO_ADJ) ? 6 : 1;
     double org[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
     unsigned wm = 0u, cm = 0u;
     float xl = 0.f;      // DW / MIXED forms: largest |low part| of a staged coordinate
     bool nf = false;     // a staged value is non-finite (staged as NaN)
-    const int nxf = nnodes * DIM, oxf = ti.n_own * DIM;
-    const int nwf = nedges * DIM, owf = ti.n_eo * DIM;
-    const int n_rounds = max(max((nxf + SBX * NTH - 1) / (SBX * NTH), (nnodes + SBC * NTH - 1) / (SBC * NTH)),
-                             (WHAT & DO_ADJ) ? (nwf + SBW * NTH - 1) / (SBW * NTH) : 0);
-    // global row of flat entry f of a list: owned rows from row0, halo rows
-    // from the tile's halo list (-1: past the end)
-    auto row_of = [&](int f, int nf_, int of_, int row0, const int32_t* hl) {
-        if (f >= nf_) return -1;
-        if (f < of_) return row0 + f / DIM;
-        return (int)hl[(f - of_) / DIM];
-    };
+    const int n_rounds = max((nnodes + SB * NTH - 1) / (SB * NTH),
+                             (WHAT & DO_ADJ) ? (nedges + SBW * NTH - 1) / (SBW * NTH) : 0);
     for (int r = 0; r < n_rounds; r++) {
-        int rx[SBX], rc[SBC], rw[SBW];
+        int vn[SB], ve[SBW];
 #pragma unroll
-        for (int u = 0; u < SBX; u++) rx[u] = row_of(r * SBX * NTH + tid + u * NTH, nxf, oxf, ti.node0 * DIM, halo);
-        if (WHAT & DO_ADJ) {
-#pragma unroll
-            for (int u = 0; u < SBC; u++) {
-                const int i = r * SBC * NTH + tid + u * NTH;
-                rc[u] = i >= nnodes ? -1 : (i < ti.n_own ? ti.node0 + i : halo[i - ti.n_own]);
-            }
-#pragma unroll
-            for (int u = 0; u < SBW; u++) rw[u] = row_of(r * SBW * NTH + tid + u * NTH, nwf, owf, ti.edge0 * DIM, hedge);
-        }
-        double xv[SBX], cv[SBC], wv[SBW];
-#pragma unroll
-        for (int u = 0; u < SBX; u++) {
-            const int f = r * SBX * NTH + tid + u * NTH;
-            if (rx[u] >= 0) xv[u] = f < oxf ? A.x[int64_t(ti.node0) * DIM + f] : A.x[int64_t(rx[u]) * DIM + (f - oxf) % DIM];
+        for (int u = 0; u < SB; u++) {
+            const int i = r * SB * NTH + tid + u * NTH;
+            vn[u] = i >= nnodes ? -1 : (i < ti.n_own ? ti.node0 + i : halo[i - ti.n_own]);
         }
         if (WHAT & DO_ADJ) {
-#pragma unroll
-            for (int u = 0; u < SBC; u++)
-                if (rc[u] >= 0) cv[u] = A.c ? A.c[rc[u]] : 0.0;
 #pragma unroll
             for (int u = 0; u < SBW; u++) {
-                const int f = r * SBW * NTH + tid + u * NTH;
-                if (rw[u] >= 0) wv[u] = f < owf ? A.w[int64_t(ti.edge0) * DIM + f] : A.w[int64_t(rw[u]) * DIM + (f - owf) % DIM];
+                const int i = r * SBW * NTH + tid + u * NTH;
+                ve[u] = i >= nedges ? -1 : (i < ti.n_eo ? ti.edge0 + i : hedge[i - ti.n_eo]);
             }
         }
+        double xv[SB][DIM], cv[SB], wv[SBW][DIM];
 #pragma unroll
-        for (int u = 0; u < SBX; u++) {
-            if (rx[u] < 0) continue;
-            const int f = r * SBX * NTH + tid + u * NTH;
-            const int d = f % DIM;
-            const double o = d == 0 ? org[0] : (d == 1 ? org[1] : org[DIM - 1]);
-            const C xc = finite_or_nan(F::coord(xv[u], o));
-            xs[f] = xc;
-            nf |= is_nan(xc);
-            if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
+        for (int u = 0; u < SB; u++) {
+            if (vn[u] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) xv[u][d] = A.x[int64_t(vn[u]) * DIM + d];
+            if (WHAT & DO_ADJ) cv[u] = A.c ? A.c[vn[u]] : 0.0;
         }
         if (WHAT & DO_ADJ) {
 #pragma unroll
-            for (int u = 0; u < SBC; u++) {
-                if (rc[u] < 0) continue;
+            for (int u = 0; u < SBW; u++)
+                if (ve[u] >= 0)
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) wv[u][d] = A.w[int64_t(ve[u]) * DIM + d];
+        }
+        if (r == 0) {
+#pragma unroll
+            for (int d = 0; d < DIM; d++)
+                if (!isfinite(org[d])) org[d] = tile_origin_component<DIM>(A.x, ti.node0, ti.n_own, d);
+        }
+#pragma unroll
+        for (int u = 0; u < SB; u++) {
+            if (vn[u] < 0) continue;
+            const int i = r * SB * NTH + tid + u * NTH;
+#pragma unroll
+            for (int d = 0; d < DIM; d++) {
+                const C xc = finite_or_nan(F::coord(xv[u][d], org[d]));
+                xs[i * DIM + d] = xc;
+                nf |= is_nan(xc);
+                if constexpr (PREC != EM_PREC_FP64) xl = fmaxf(xl, fabsf(xc.l));
+            }
+            if (WHAT & DO_ADJ) {
                 const V c1 = finite_or_nan(F::from_double(cv[u]));
-                cs[r * SBC * NTH + tid + u * NTH] = c1;
+                cs[i] = c1;
                 nf |= is_nan(c1);
                 cm = max(cm, FX::mag(c1));
             }
+        }
+        if (WHAT & DO_ADJ) {
 #pragma unroll
             for (int u = 0; u < SBW; u++) {
-                if (rw[u] < 0) continue;
-                const V w1 = finite_or_nan(F::from_double(wv[u]));
-                ws[r * SBW * NTH + tid + u * NTH] = w1;
-                nf |= is_nan(w1);
-                wm = max(wm, FX::mag(w1));
+                if (ve[u] < 0) continue;
+                const int i = r * SBW * NTH + tid + u * NTH;
+#pragma unroll
+                for (int d = 0; d < DIM; d++) {
+                    const V w1 = finite_or_nan(F::from_double(wv[u][d]));
+                    ws[i * DIM + d] = w1;
+                    nf |= is_nan(w1);
+                    wm = max(wm, FX::mag(w1));
+                }
             }
         }
     }
