@@ -229,7 +229,7 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     // their gathers, and converts last, so a round costs two dependent trips to
     // L2 / HBM however many lists it covers.  The tile origin is loaded with
     // the indices and only replaced when it is not finite (rare).
-    constexpr int SB = 2, SBW = (WHAT & DO_ADJ) ? 6 : 1;
+    constexpr int SB = NTH > NT ? 1 : 2, SBW = (WHAT & DO_ADJ) ? 6 : 1;
     double org[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; d++) org[d] = A.x[int64_t(ti.node0) * DIM + d];
