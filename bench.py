@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--prec", default=None, help="fp64 | dw | mixed")
     p.add_argument("--tile-nodes", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--fwd-only", action="store_true",
+                   help="timed steps run the forward alone (n, V, bnormal) on the tiled or gather path; "
+                        "for profiling the forward kernel (the end-to-end part still runs the fused step)")
     p.add_argument("--no-forms", action="store_true", help="skip the per-form comparison timings")
     p.add_argument("--cpu-sample-elems", type=int, default=1_500_000)
     p.add_argument("--cpu-reps", type=int, default=10)
@@ -479,7 +482,10 @@ def run_ours(args):
         if path in ("gather", "tiled"):
             if ev is not None:
                 ev[0].record(stream)
-            api.edge_metrics_fused(topo, x_, w_, c_, prec, out=outs, path=path)
+            if args.fwd_only:
+                api.edge_metrics(topo, x_, prec, path, out=outs[:3])
+            else:
+                api.edge_metrics_fused(topo, x_, w_, c_, prec, out=outs, path=path)
             if ev is not None:
                 ev[1].record(stream)
         else:
@@ -529,7 +535,8 @@ def run_ours(args):
     # dominant kernel: the fused gather kernel, or the forward element kernel
     if path in ("gather", "tiled"):
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
-        what, kname = "fused", f"{'k_stile' if path == 'tiled' else 'k_tile'}<3,{prec},fwd+adj>"
+        what = "fwd" if args.fwd_only else "fused"
+        kname = f"{'k_stile' if path == 'tiled' else 'k_tile'}<3,{prec},{'fwd' if args.fwd_only else 'fwd+adj'}>"
     else:
         call_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(K)]
         what, kname = "fwd", f"k_fwd_atomic3<{prec}>"
@@ -715,7 +722,8 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "metric": METRIC + (" [forward only]" if args.fwd_only and path in ("gather", "tiled") else ""),
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "dw": "f32x2+i64 (FP64-accurate)", "mixed": "f32",
                       "mixed_comp32": "f32"}.get(prec, prec),
