@@ -35,6 +35,10 @@
  *   - Coordinates are float64 [n_nodes][dim], row-major.
  *   - Node, element, edge and face counts must be below 2^31 - 1 (int32
  *     indices); byte offsets are size_t.
+ *   - A grid has at least one node, one element and (once built) one edge:
+ *     entry points that take a grid refuse zero counts with EM_ERR_ARG
+ *     before any device work, since an empty grid has nothing to compute
+ *     (em_check_elements alone accepts n_elems == 0 and reports no errors).
  *   - Every function returns an int status: EM_OK (0) or a negative EM_ERR_*
  *     code.  em_last_error() returns a message for the calling thread's last
  *     failure.  No C++ exception crosses the ABI and no kernel traps: device-

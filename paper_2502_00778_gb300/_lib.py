@@ -16,7 +16,8 @@ ERRORS = {
 }
 
 PLAN_INFO_LEN = 32
-PLAN_INFO = {"tile_nodes": 0, "tiles": 1, "rec_nodes": 20, "rec_edges": 21, "rec_bnodes": 22}
+PLAN_INFO = {"tile_nodes": 0, "tiles": 1, "max_edge_valence": 13, "max_node_valence": 14, "rec_nodes": 20,
+             "rec_edges": 21, "rec_bnodes": 22}
 
 PREC = {"fp64": 0, "dw": 1, "mixed": 2, "mixed_comp32": 3}
 PATH = {"atomic": 0, "gather": 1, "csr": 2, "tiled": 3}

@@ -347,38 +347,60 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     __syncthreads();
 
     // ---- scales: no accumulated sum can reach 2^TOP -------------------------
-    // Each bound is a product (or a sum of three products) of factors with
-    // power-of-two upper bounds, so its exponent is a sum of exponents: every
-    // thread derives the same scales with integer arithmetic, with no FP64
-    // instruction and no further barrier.  (Rounding each factor up to a power
-    // of two gives away at most a few of the 62 bits.)  A partial sum of a
-    // tile holds at most as many contributions as the full sum, so the grid's
-    // valences bound it too.
+    // Each bound is a product (or a sum of three products) of upper bounds,
+    // evaluated as float mantissas rounded up times powers of two: every
+    // thread derives the same scales with no FP64 instruction and no further
+    // barrier, and each scale gives away less than one of the 62 bits plus
+    // the 2^-12 margin below.  A partial sum of a tile holds at most as many
+    // contributions as the full sum, so the grid's valences bound it too.
     constexpr int TP = FX::TOP, LO = FX::LO, HI = FX::HI;
-    // DW / MIXED: Lx <= b0 (1 + 2^-20) + 2 b3 < 2^(max(E0, E3) + 2), with b0 < 2^E0
-    // bounding the high-part extent (slot 0) and b3 < 2^E3 the low parts (slot 3)
     constexpr int NW = NTH / 32;
-    const int eL = PREC == EM_PREC_FP64 ? key_exp(red_max(wred, 0, NW))
-                                        : max(key_exp(red_max(wred, 0, NW)), key_exp(red_max(wred, 3, NW))) + 2;
-    const int eKe = 32 - __clz(A.val_e > 1 ? A.val_e : 1), eKv = 32 - __clz(A.val_v > 1 ? A.val_v : 1);
-    int eg = 0;
+    // Lx.  FP64 form: slot 0 bounds the computed differences, rounded to
+    // nearest, so the exact ones too.  DW / MIXED: |a - b| <= |a.h - b.h| +
+    // |a.l| + |b.l| <= fl(a.h - b.h) (1 + 2^-23) + 2 max|low part| (slot 3).
+    Ub uL = ub_key(red_max(wred, 0, NW));
+    if constexpr (PREC != EM_PREC_FP64) {
+        Ub l3 = ub_key(red_max(wred, 3, NW));
+        l3.e += 1;
+        uL = ub_add(ub_scale(uL, 1.0f + 0x1p-23f), l3);
+    }
+    // mantissa products m (>= 1, rounded up) and exponent sums e: the bound
+    // is below m 2^e; powers of two go to e
+    const float mL2 = __fmul_ru(uL.m, uL.m), mL3 = __fmul_ru(mL2, uL.m);
+    // contribution counts (the launcher refuses valences above 340 / 170, so
+    // these floats are exact), with a 2^-12 margin for the rounding of the
+    // computed contributions against the exact quantities bounded here
+    const float Ke = __fmul_ru((float)(max(A.val_e, 1) + 1), 1.0f + 0x1p-12f);
+    const float Kv = __fmul_ru((float)(max(A.val_v, 1) + 1), 1.0f + 0x1p-12f);
+    auto room = [&](float m, int e) { return TP - (e + ub_bits(m)); };
+    int u_g = HI;
     if (WHAT & DO_ADJ) {
-        // |w|, |c|, |bw| < 2^Ew, 2^Ec, 2^Eb
-        const int Ew = key_exp(red_max(wred, 1, NW)), Ec = key_exp(red_max(wred, 2, NW));
-        const int Eb = A.bwa.bw ? key_exp(*A.bwa.key) : -2000;
-        if (DIM == 3)   // 12 (16 |w| Lx + 8 |c| Lx^2 + 16 |bw| Lx) 2 Kv: the 3D sums hold 12 g
-            eg = max(max(4 + Ew + eL, 3 + Ec + 2 * eL), 4 + Eb + eL) + 2 + 1 + eKv + 4;
-        else            // (4 |w| + 4 |c| Lx + 4 |bw|) 2 Kv
-            eg = max(max(2 + Ew, 2 + Ec + eL), 2 + Eb) + 2 + 1 + eKv;
+        // |w|, |c|, |bw| below W, C, B
+        const Ub W = ub_key(red_max(wred, 1, NW)), C = ub_key(red_max(wred, 2, NW));
+        Ub T;
+        if (DIM == 3) {   // 12 (16 |w| Lx + 8 |c| Lx^2 + 16 |bw| Lx) 2 Kv: the 3D sums hold 12 g
+            T = ub_add(ub_norm(__fmul_ru(W.m, uL.m), W.e + uL.e + 4), ub_norm(__fmul_ru(C.m, mL2), C.e + 2 * uL.e + 3));
+            if (A.bwa.bw) {
+                const Ub B = ub_key(*A.bwa.key);
+                T = ub_add(T, ub_norm(__fmul_ru(B.m, uL.m), B.e + uL.e + 4));
+            }
+            u_g = room(__fmul_ru(__fmul_ru(T.m, Kv), 3.0f), T.e + 3);
+        } else {          // (4 |w| + 4 |c| Lx + 4 |bw|) 2 Kv
+            T = ub_add(W, ub_norm(__fmul_ru(C.m, uL.m), C.e + uL.e));
+            if (A.bwa.bw) T = ub_add(T, ub_key(*A.bwa.key));
+            u_g = room(__fmul_ru(T.m, Kv), T.e + 3);
+        }
     }
     // 3D: |N_i| components <= 2 Lx^2, |det| <= 3 sqrt(3) Lx^3 < 8 Lx^3,
-    // |n_B| <= 8 Lx^2 with up to 3 boundary faces per element at a node;
-    // 2D: |n_i| <= 2 Lx, |det| <= 2 Lx^2, boundary edge <= 2 Lx
-    const int u_e = TP - (DIM == 3 ? 5 + 2 * eL + eKe : 3 + eL + eKe);
-    const int u_v = TP - (DIM == 3 ? 3 + 3 * eL + eKv : 4 + 2 * eL + eKv);
-    const int u_b = TP - (DIM == 3 ? 5 + 2 * eL + eKv : 3 + eL + eKv);
+    // |n_B| <= 8 Lx^2 with up to 3 boundary faces per element at a node; the
+    // factors 2^5, 2^3, 2^5 cover the shares and the sums' 12 n, 24 V,
+    // 3 bnormal; 2D: |n_i| <= 2 Lx, |det| <= 2 Lx^2, boundary edge <= 2 Lx
+    // (factors 2^3, 2^4, 2^3)
+    const int u_e = DIM == 3 ? room(__fmul_ru(mL2, Ke), 2 * uL.e + 5) : room(__fmul_ru(uL.m, Ke), uL.e + 3);
+    const int u_v = DIM == 3 ? room(__fmul_ru(mL3, Kv), 3 * uL.e + 3) : room(__fmul_ru(mL2, Kv), 2 * uL.e + 4);
+    const int u_b = DIM == 3 ? room(__fmul_ru(mL2, Kv), 2 * uL.e + 5) : room(__fmul_ru(uL.m, Kv), uL.e + 3);
     const int sg_e = sg_clamp(u_e, LO, HI), sg_v = sg_clamp(u_v, LO, HI), sg_b = sg_clamp(u_b, LO, HI);
-    const int sg_g = (WHAT & DO_ADJ) ? sg_clamp(TP - eg, LO, HI) : 0;
+    const int sg_g = (WHAT & DO_ADJ) ? sg_clamp(u_g, LO, HI) : 0;
     // Element extents outside the form's range (a scale outside [LO, HI]:
     // the values would overflow the fixed point, or lose the digits the
     // contract needs) make every output of the tile NaN instead of silently
@@ -388,7 +410,7 @@ __device__ __forceinline__ void run_stile(const SArgs& A, int t, char* smem, con
     // Non-finite staged values mark the tile for the poison pass below.
     const bool lx0 = red_max(wred, 0, NW) == 0u;
     const bool range_bad = (!lx0 && (u_e < LO || u_e > HI || u_v < LO || u_v > HI || u_b < LO || u_b > HI)) ||
-                           ((WHAT & DO_ADJ) && TP - eg < LO);
+                           ((WHAT & DO_ADJ) && u_g < LO);
     const bool nf_tile = red_max(wred, 4, NW) != 0u;
     if ((tid >> 5) == (NTH >> 5) - 1) pf(tid & 31);
 

@@ -228,6 +228,52 @@ __device__ __forceinline__ unsigned mkey(double v) {
 }
 __device__ __forceinline__ int key_exp(unsigned k) { return (int)(((k + 1u) >> 20) & 0x7ffu) - 1022; }
 
+// ---- upper bounds for the fixed-point scales --------------------------------
+// A bound m 2^e with a float mantissa m in [1, 2) and an integer exponent, so
+// that it covers any double range.  A key gives the bound of the double whose
+// upper word follows it (20 mantissa bits, exact in a float); products and
+// sums round up.  Taking the exponent of a whole product gives away less than
+// one bit, where rounding each factor to a power of two gave away up to one
+// bit per factor.  Integer and FP32 instructions only.
+struct Ub {
+    float m;
+    int e;
+};
+
+// m >= 1 (a normal float) to [1, 2), adjusting e; exact
+__device__ __forceinline__ Ub ub_norm(float m, int e) {
+    const unsigned b = __float_as_uint(m);
+    const int k = (int)((b >> 23) & 0xffu) - 127;
+    return {__uint_as_float(b - ((unsigned)k << 23)), e + k};
+}
+
+// above every value whose key is k (k below the key of infinity)
+__device__ __forceinline__ Ub ub_key(unsigned k) {
+    const unsigned n = k + 1u;
+    const int ex = (int)(n >> 20);
+    if (ex == 0) return {1.0f, -1022};   // every subnormal double is below 2^-1022
+    return {__uint_as_float(0x3f800000u | ((n & 0xfffffu) << 3)), ex - 1023};
+}
+
+// a * c for a float c >= 1 (a small integer or 1 + 2^-k: exact)
+__device__ __forceinline__ Ub ub_scale(Ub a, float c) { return ub_norm(__fmul_ru(a.m, c), a.e); }
+__device__ __forceinline__ Ub ub_mul(Ub a, Ub b) { return ub_norm(__fmul_ru(a.m, b.m), a.e + b.e); }
+__device__ __forceinline__ Ub ub_add(Ub a, Ub b) {
+    if (a.e < b.e) {
+        const Ub t = a;
+        a = b;
+        b = t;
+    }
+    const int d = a.e - b.e;
+    // b.m 2^-d (exact for d <= 60; 2^-60 bounds it beyond)
+    const float bs = d > 60 ? 0x1p-60f : __fmul_ru(b.m, __uint_as_float((unsigned)(127 - d) << 23));
+    return ub_norm(__fadd_ru(a.m, bs), a.e);
+}
+// the least e' with m 2^e < 2^e'
+__device__ __forceinline__ int ub_exp(Ub a) { return a.e + 1; }
+// the least k with m < 2^k, for a normal float m >= 1
+__device__ __forceinline__ int ub_bits(float m) { return (int)((__float_as_uint(m) >> 23) & 0xffu) - 126; }
+
 
 template <int PREC>
 struct Fix;
@@ -284,16 +330,16 @@ struct Fix<EM_PREC_MIXED> {
 
 // block-wide maxima without a cleared slot: each warp writes its maximum to
 // its own entry of slot s (16 entries per slot), and readers take the max of
-// the entries after a barrier
+// the entries after a barrier, lane w reading warp w's entry (whole warps
+// only: every lane of the warp calls red_max)
 constexpr int RED_WARPS = 16;
 __device__ __forceinline__ void block_max(unsigned* wred, int s, unsigned v) {
     v = __reduce_max_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0) wred[s * RED_WARPS + (threadIdx.x >> 5)] = v;
 }
 __device__ __forceinline__ unsigned red_max(const unsigned* wred, int s, int nwarps) {
-    unsigned m = 0u;
-    for (int w = 0; w < nwarps; w++) m = max(m, wred[s * RED_WARPS + w]);
-    return m;
+    const int lane = (int)(threadIdx.x & 31);
+    return __reduce_max_sync(0xffffffffu, lane < nwarps ? wred[s * RED_WARPS + lane] : 0u);
 }
 
 // ---- L2 prefetch of a later tile's inputs -----------------------------------

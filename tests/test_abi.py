@@ -134,3 +134,35 @@ def test_partial_entry_point_rejects_bad_arguments(lib):
     L.em_last_error(buf, 256)
     assert b"needs w" in buf.value
     assert L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 1, fake, null, null, null, null, null, null, null) == -1
+
+
+def test_empty_grids_are_refused_before_device_work(lib):
+    """A grid needs at least one node, one element and one edge: zero counts
+    fail with EM_ERR_ARG before any device call."""
+    import paper_2502_00778_gb300 as p
+    L = p.load()
+    buf = ctypes.create_string_buffer(256)
+    sz = ctypes.c_size_t(0)
+    cnt = (ctypes.c_int64 * 3)()
+    for nv, ne in ((10, 0), (0, 10)):
+        st = L.em_edge_build(3, nv, ne, None, None, None, ctypes.byref(sz), None, 0, None, None, None, None, None, 0,
+                             None, 0, cnt, None)
+        assert st == -1
+    psz = ctypes.c_size_t(0)
+    info = (ctypes.c_int64 * p._lib.PLAN_INFO_LEN)()
+    st = L.em_plan_build(3, 10, 0, None, None, 6, None, 0, None, None, 0, None, 128, None, ctypes.byref(sz), None,
+                         ctypes.byref(psz), info, None)
+    assert st == -1
+    m = p._lib.EmMesh()
+    m.elems = m.elem2edge = m.edges = 4096   # never dereferenced: validation fails first
+    fake = ctypes.c_void_p(4096)
+    for nv, ne, nedges in ((4, 0, 6), (0, 1, 6), (4, 1, 0)):
+        m.dim, m.n_nodes, m.n_elems, m.n_edges = 3, nv, ne, nedges
+        st = L.em_edge_metrics(ctypes.byref(m), 0, 0, fake, fake, fake, fake, None, ctypes.byref(sz), None)
+        assert st == -1
+        L.em_last_error(buf, 256)
+        assert b"positive" in buf.value
+        st = L.em_edge_metrics_partial(ctypes.byref(m), 0, 0, 0, fake, None, None, fake, fake, fake, None, None)
+        assert st == -1
+        L.em_last_error(buf, 256)
+        assert b"positive" in buf.value
