@@ -141,9 +141,20 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def sources_sha1(ent):
+    """SHA-1 over the bytes of an entry's source files, in the listed order:
+    `sources` (the kernel's translation unit and the headers holding its
+    device code) or, in older entries, the single `source`."""
+    import hashlib
+    h = hashlib.sha1()
+    for rel in ent.get("sources") or [ent["source"]]:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(kernel, tile=None):
     """DRAM bytes per launch of `kernel` (at tile size `tile`) from the
-    committed ncu summary, if the summary was taken on the current source of
+    committed ncu summary, if the summary was taken on the current sources of
     that kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -155,10 +166,7 @@ def kernel_traffic(kernel, tile=None):
             return None
         if not ent:
             return None
-        src = os.path.join(ROOT, ent["source"])
-        import hashlib
-        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if h != ent.get("source_sha1"):
+        if sources_sha1(ent) != ent.get("source_sha1"):
             return None
         return ent["dram_bytes_per_launch"] * ent.get("scale_to_full", 1.0)
     except Exception:
@@ -243,7 +251,7 @@ def cpu_comparisons(m, args):
 def fp64_ops(kernel):
     """FP64 instructions per element of a native-FP64 kernel, counted by ncu
     (thread-level DADD + DMUL + DFMA executed), from the committed summary,
-    if it was taken on the current source of that kernel."""
+    if it was taken on the current sources of that kernel."""
     p = os.path.join(ROOT, "profiles", "fp64_ops.json")
     if not os.path.exists(p):
         return None
@@ -251,9 +259,7 @@ def fp64_ops(kernel):
         ent = json.load(open(p)).get(kernel)
         if not ent:
             return None
-        import hashlib
-        src = os.path.join(ROOT, ent["source"])
-        if hashlib.sha1(open(src, "rb").read()).hexdigest() != ent.get("source_sha1"):
+        if sources_sha1(ent) != ent.get("source_sha1"):
             return None
         return float(ent["fp64_ops_per_element"])
     except Exception:

@@ -65,18 +65,52 @@ def test_kernel_traffic_requires_the_captured_source(tmp_path, monkeypatch):
     assert bench.kernel_traffic("other", 256) is None
     src.write_text("// kernel source, changed\n")
     assert bench.kernel_traffic("kern", 256) is None         # source changed since the capture
+    # several sources: a change in a header with device code drops the figure too
+    hdr = tmp_path / "k.cuh"
+    hdr.write_text("// device helpers\n")
+    entry = {"sources": ["k.cu", "k.cuh"], "dram_bytes_per_launch": 1000, "tile_nodes": 256, "scale_to_full": 1.0}
+    entry["source_sha1"] = hashlib.sha1(src.read_bytes() + hdr.read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"kern|tile256": entry}))
+    assert bench.kernel_traffic("kern", 256) == pytest.approx(1000.0)
+    hdr.write_text("// device helpers, changed\n")
+    assert bench.kernel_traffic("kern", 256) is None
+
+
+def _device_sources(cu):
+    """The .cu file and every csrc header it includes, directly or through
+    other csrc headers (the public header holds no device code)."""
+    import re
+    d = os.path.dirname(cu)
+    seen, todo = [], [cu]
+    while todo:
+        f = todo.pop(0)
+        if f in seen:
+            continue
+        seen.append(f)
+        for inc in re.findall(r'#include "([^"/]+)"', open(os.path.join(ROOT, f)).read()):
+            todo.append(os.path.join(d, inc))
+    return sorted(seen)
+
+
+def test_committed_figures_cover_the_kernels_includes():
+    for name in ("traffic.json", "fp64_ops.json"):
+        j = json.load(open(os.path.join(ROOT, "profiles", name)))
+        for key, ent in j.items():
+            if key.startswith("_"):
+                continue
+            assert sorted(ent["sources"]) == _device_sources(ent["sources"][0]), (name, key)
 
 
 def test_committed_traffic_matches_its_source():
-    """Every committed traffic figure names a source file that exists and
-    carries that file's current checksum (otherwise the benchmark drops it)."""
+    """Every committed traffic figure names source files that exist and
+    carries their current checksum (otherwise the benchmark drops it)."""
     j = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     for key, ent in j.items():
         if key.startswith("_"):      # notes
             continue
-        p = os.path.join(ROOT, ent["source"])
-        assert os.path.exists(p), key
-        assert hashlib.sha1(open(p, "rb").read()).hexdigest() == ent["source_sha1"], key
+        for rel in ent["sources"]:
+            assert os.path.exists(os.path.join(ROOT, rel)), (key, rel)
+        assert bench.sources_sha1(ent) == ent["source_sha1"], key
         assert ent["dram_bytes_per_launch"] > 0 and ent["scale_to_full"] > 0
 
 
@@ -89,8 +123,7 @@ def test_committed_fp64_counts_match_their_source():
     assert "k_fwd_atomic3<fp64>" in kernels
     for key in kernels:
         ent = j[key]
-        p = os.path.join(ROOT, ent["source"])
-        assert hashlib.sha1(open(p, "rb").read()).hexdigest() == ent["source_sha1"], key
+        assert bench.sources_sha1(ent) == ent["source_sha1"], key
         per = ent["fp64_pipe_thread_inst"] / ent["elements"]
         assert abs(per - ent["fp64_ops_per_element"]) < 0.01
         assert bench.fp64_ops(key) == pytest.approx(ent["fp64_ops_per_element"])
