@@ -49,6 +49,26 @@ def _require_cuda(*ts):
             raise ValueError("edge-metrics tensors must be CUDA tensors")
 
 
+def _check_sizes(topo, **named):
+    """Host-side checks before any launch.  The library reads and writes its
+    arrays through plain pointers, so a tensor with the wrong number of
+    elements would make a kernel access memory outside it; a tensor whose
+    memory the library uses as is (an output written in place, or a batched
+    input whose address is kept) must be contiguous float64; and every tensor
+    must live on the grid's device.  `named` maps a name to (tensor or None,
+    the number of elements the grid needs, whether its memory is used as is)."""
+    dev = topo.elems.device
+    for name, (t, count, as_is) in named.items():
+        if t is None:
+            continue
+        if t.numel() != count:
+            raise ValueError(f"{name} has {t.numel()} elements; this grid needs {count}")
+        if as_is and (t.dtype != torch.float64 or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 tensor: the library uses its memory as is")
+        if t.device != dev:
+            raise ValueError(f"{name} is on {t.device}; the grid's arrays are on {dev}")
+
+
 class Topology:
     """Integer topology from em_edge_build (+ optional gather plan)."""
 
@@ -177,6 +197,10 @@ def _mesh_ref(topo):
 def edge_metrics(topo: Topology, x: torch.Tensor, precision: str = "fp64", path: str = "atomic", out=None):
     """Forward: (n_edge [Ne,dim], vol [Nv], bnormal [Nbn,dim]) as float64 CUDA tensors."""
     L = load()
+    d = topo.dim
+    n0, v0, b0 = out if out is not None else (None, None, None)
+    _check_sizes(topo, x=(x, topo.n_nodes * d, False), n_edge=(n0, topo.n_edges * d, True),
+                 vol=(v0, topo.n_nodes, True), bnormal=(b0, topo.n_bnodes * d, True))
     _require_cuda(x)
     x = x.contiguous().to(torch.float64)
     dim, dev = topo.dim, x.device
@@ -202,6 +226,9 @@ def edge_metrics_adjoint(topo: Topology, x, w, c=None, precision: str = "fp64", 
     bw (boundary-normal weights, [n_bnodes, dim] in topo.bnode order) is
     optional and supported on the atomic and tiled paths."""
     L = load()
+    d = topo.dim
+    _check_sizes(topo, x=(x, topo.n_nodes * d, False), w=(w, topo.n_edges * d, False), c=(c, topo.n_nodes, False),
+                 bw=(bw, topo.n_bnodes * d, False), grad=(out, topo.n_nodes * d, True))
     _require_cuda(x, w, c, bw)
     x = x.contiguous().to(torch.float64)
     w = w.contiguous().to(torch.float64)
@@ -226,6 +253,12 @@ def edge_metrics_fused(topo: Topology, x, w, c=None, precision: str = "fp64", ou
     "gather" = deterministic ordered gather, "tiled" = shared-memory scatter;
     bw as in edge_metrics_adjoint, tiled path only)."""
     L = load()
+    d = topo.dim
+    n0, v0, b0, g0 = out if out is not None else (None, None, None, None)
+    _check_sizes(topo, x=(x, topo.n_nodes * d, False), w=(w, topo.n_edges * d, False), c=(c, topo.n_nodes, False),
+                 bw=(bw, topo.n_bnodes * d, False), n_edge=(n0, topo.n_edges * d, True),
+                 vol=(v0, topo.n_nodes, True), bnormal=(b0, topo.n_bnodes * d, True),
+                 grad=(g0, topo.n_nodes * d, True))
     _require_cuda(x, w, c, bw)
     x = x.contiguous().to(torch.float64)
     w = w.contiguous().to(torch.float64)
@@ -258,6 +291,8 @@ def edge_metrics_partial(topo: Topology, x, elem_range, w=None, c=None, precisio
     not asked for.  Summing the tuples of ranges that cover the grid gives the
     full result up to rounding order (sharding.reduce_partials)."""
     L = load()
+    d = topo.dim
+    _check_sizes(topo, x=(x, topo.n_nodes * d, False), w=(w, topo.n_edges * d, False), c=(c, topo.n_nodes, False))
     _require_cuda(x, w, c)
     lo, hi = (int(v) for v in elem_range)
     x = x.contiguous().to(torch.float64)
@@ -280,6 +315,7 @@ def edge_metrics_partial(topo: Topology, x, elem_range, w=None, c=None, precisio
 def edge_volume(topo: Topology, x, n_edge):
     """Edge-based dual volume (Sec. 4.1) from lumped directed-area vectors."""
     L = load()
+    _check_sizes(topo, x=(x, topo.n_nodes * topo.dim, False), n_edge=(n_edge, topo.n_edges * topo.dim, False))
     _require_cuda(x, n_edge)
     x = x.contiguous().to(torch.float64)
     n_edge = n_edge.contiguous().to(torch.float64)
@@ -296,6 +332,7 @@ def edge_volume(topo: Topology, x, n_edge):
 def edge_areas_traditional(topo: Topology, x, out=None):
     """n_jk by the traditional dual-face construction (Sec. 3.1), FP64 atomics."""
     L = load()
+    _check_sizes(topo, x=(x, topo.n_nodes * topo.dim, False), n_edge=(out, topo.n_edges * topo.dim, True))
     _require_cuda(x)
     x = x.contiguous().to(torch.float64)
     n = out if out is not None else torch.empty((topo.n_edges, topo.dim), dtype=torch.float64, device=x.device)
@@ -307,6 +344,9 @@ def edge_areas_traditional(topo: Topology, x, out=None):
 def edge_residual(topo: Topology, F, n_edge, bnormal):
     """Edge-loop residual with central fluxes (Sec. 2) for nodal fluxes F."""
     L = load()
+    d = topo.dim
+    _check_sizes(topo, F=(F, topo.n_nodes * d, False), n_edge=(n_edge, topo.n_edges * d, False),
+                 bnormal=(bnormal, topo.n_bnodes * d, False))
     _require_cuda(F, n_edge, bnormal)
     F = F.contiguous().to(torch.float64)
     n_edge = n_edge.contiguous().to(torch.float64)
@@ -387,6 +427,8 @@ class Batch:
             raise ValueError("all grids of a batch must have the same dimension")
         if any(t.plan is None for t in topos):
             raise ValueError("every grid needs a plan (plan_build)")
+        if not (len(xs) == len(ws) == len(cs) == len(topos)):
+            raise ValueError("one x, w and c per grid")
         dev = xs[0].device
         self.topos, self.xs, self.ws, self.cs = topos, xs, ws, cs
         self.precision = precision
@@ -396,6 +438,8 @@ class Batch:
         items = (_lib.EmBatchItem * len(topos))()
         for i, (t, x, w, c) in enumerate(zip(topos, xs, ws, cs)):
             d = t.dim
+            _check_sizes(t, **{f"xs[{i}]": (x, t.n_nodes * d, True), f"ws[{i}]": (w, t.n_edges * d, True),
+                               f"cs[{i}]": (c, t.n_nodes, True)})
             o = (torch.empty((t.n_edges, d), dtype=torch.float64, device=dev),
                  torch.empty(t.n_nodes, dtype=torch.float64, device=dev),
                  torch.empty((t.n_bnodes, d), dtype=torch.float64, device=dev),
